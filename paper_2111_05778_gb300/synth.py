@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds no polygonization arithmetic: it only draws the parameters
+of the shapes the benchmarks and tests polygonize, with numpy's PCG64
+``default_rng``.  Every value is rounded to float32 once, so the CUDA path
+(float32) and the FP64 oracle see exactly the same function.
+
+Shapes (the paper's learned SDBs and scenes are not available, Sec. 5):
+
+* ``sphere_prims``: one sphere, f = |p - c| - r.
+* ``csg_prims(seed)``: the union (min, Sec. 4.3) of 24 spheres and 8 randomly
+  rotated tori, minus 4 axis-aligned boxes (max with -d_box).
+* ``mlp_params(seed, width)``: f(p) = (|p| - 0.6 + 0.1 g(p)) / 1.1 where g is
+  a ReLU MLP 3 -> W -> ... -> W -> 1 (six W-wide layers) with Gaussian weights,
+  each matrix divided by its largest singular value (so g and f are
+  1-Lipschitz, i.e. signed distance bounds, Sec. 1) and N(0, 0.01^2) biases.
+* ``batch_items()``: 64 (kind, seed, N, width) items mixing both generators.
+
+Primitive rows are 17 float64 numbers:
+``type, op, cx, cy, cz, p0, p1, p2, rot[9]`` with type 0 sphere (p0 = r),
+1 torus around the local y axis (p0 = R, p1 = r), 2 box (half sizes p0..p2);
+op 0 union, 1 subtract, 2 intersect, applied as a left fold; ``rot`` maps
+world offsets to the primitive's local frame (row-major).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PRIM_STRIDE = 17
+SPHERE, TORUS, BOX = 0, 1, 2
+UNION, SUBTRACT, INTERSECT = 0, 1, 2
+
+MLP_R0, MLP_ALPHA, MLP_BETA = 0.6, 0.1, 1.1
+MLP_NMID = 5  # W x W layers between the 3 -> W input layer and the W -> 1 output
+
+
+def _f32(a):
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+def prim_row(kind, op, centre, params, rot=None) -> np.ndarray:
+    r = np.zeros(PRIM_STRIDE, np.float64)
+    r[0], r[1] = kind, op
+    r[2:5] = centre
+    p = np.zeros(3)
+    p[: len(params)] = params
+    r[5:8] = p
+    r[8:17] = (np.eye(3) if rot is None else np.asarray(rot, np.float64)).ravel()
+    return _f32(r)
+
+
+def sphere_prims(r=0.5, centre=(0.0, 0.0, 0.0)) -> np.ndarray:
+    return prim_row(SPHERE, UNION, centre, [r])[None, :]
+
+
+def half_space_prims(normal, offset, big=64.0) -> np.ndarray:
+    """The half-space n.p <= offset as a huge box whose one face is the plane
+    n.p = offset (the exact box distance then equals the plane distance of
+    Eq. 5 everywhere inside the polygonization volume)."""
+    n = np.asarray(normal, np.float64)
+    n = n / np.linalg.norm(n)
+    # build a rotation whose first row is n (local x axis = plane normal)
+    a = np.eye(3)[np.argmin(np.abs(n))]
+    u = np.cross(n, a)
+    u /= np.linalg.norm(u)
+    v = np.cross(n, u)
+    rot = np.stack([n, u, v])
+    centre = n * (offset - big)
+    return prim_row(BOX, UNION, centre, [big, big, big], rot)[None, :]
+
+
+def _quat_rot(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array(
+        [
+            [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+            [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+            [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+        ]
+    )
+
+
+def csg_prims(seed: int, n_sphere=24, n_torus=8, n_box=4) -> np.ndarray:
+    """CSG scene: draw order spheres (centre U[-0.7,0.7]^3, r U[0.05,0.2]),
+    tori (centre, R U[0.1,0.3], r U[0.02,0.06], rotation from a normalised
+    4-D Gaussian quaternion), boxes (centre, half sizes U[0.05,0.15] each,
+    axis-aligned, subtracted)."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for _ in range(n_sphere):
+        c = rng.uniform(-0.7, 0.7, 3)
+        r = rng.uniform(0.05, 0.2)
+        rows.append(prim_row(SPHERE, UNION, c, [r]))
+    for _ in range(n_torus):
+        c = rng.uniform(-0.7, 0.7, 3)
+        R = rng.uniform(0.1, 0.3)
+        r = rng.uniform(0.02, 0.06)
+        rot = _quat_rot(rng.standard_normal(4))
+        rows.append(prim_row(TORUS, UNION, c, [R, r], rot))
+    for _ in range(n_box):
+        c = rng.uniform(-0.7, 0.7, 3)
+        hs = rng.uniform(0.05, 0.15, 3)
+        rows.append(prim_row(BOX, SUBTRACT, c, hs))
+    return np.stack(rows)
+
+
+def mlp_param_count(width: int, nmid: int = MLP_NMID) -> int:
+    return 3 * width + width + nmid * (width * width + width) + width + 1
+
+
+def mlp_layers(seed: int, width: int = 256, nmid: int = MLP_NMID):
+    """[(W_l, b_l)] float32, shapes (W,3),(W,W)*nmid,(1,W)."""
+    rng = np.random.default_rng(seed)
+    shapes = [(width, 3)] + [(width, width)] * nmid + [(1, width)]
+    layers = []
+    for out_d, in_d in shapes:
+        W = rng.standard_normal((out_d, in_d))
+        b = rng.normal(0.0, 0.01, out_d)
+        sig = np.linalg.svd(W, compute_uv=False)[0]
+        layers.append(((W / sig).astype(np.float32), b.astype(np.float32)))
+    return layers
+
+
+def pack_layers(layers) -> np.ndarray:
+    """Flat float32 vector W0 b0 {W b}*nmid wout bout (row-major)."""
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers]).astype(np.float32)
+
+
+def unpack_layers(vec, width: int, nmid: int = MLP_NMID):
+    vec = np.asarray(vec)
+    shapes = [(width, 3)] + [(width, width)] * nmid + [(1, width)]
+    out, o = [], 0
+    for od, id_ in shapes:
+        W = vec[o : o + od * id_].reshape(od, id_)
+        o += od * id_
+        b = vec[o : o + od]
+        o += od
+        out.append((W, b))
+    return out
+
+
+def mlp_params(seed: int, width: int = 256, nmid: int = MLP_NMID) -> np.ndarray:
+    return pack_layers(mlp_layers(seed, width, nmid))
+
+
+BATCH_NS = (128, 256, 384, 512, 768, 1024)
+BATCH_WIDTHS = (64, 128, 256)
+
+
+def batch_items(n: int = 64):
+    """(kind, seed, N, width) for seeds 0..n-1: even seeds CSG, odd seeds MLP;
+    N and width drawn from default_rng(10000 + seed)."""
+    items = []
+    for s in range(n):
+        rng = np.random.default_rng(10000 + s)
+        N = int(rng.choice(BATCH_NS))
+        W = int(rng.choice(BATCH_WIDTHS))
+        items.append(("csg" if s % 2 == 0 else "mlp", s, N, W))
+    return items
+
+
+def uniform_points(seed: int, n: int, lo=-1.0, hi=1.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, (n, 3)).astype(np.float32)
