@@ -1,0 +1,341 @@
+"""Benchmark of the grid-hopping polygonizer on one GB300 (or N replicas).
+
+Workload: the neural SDB f(p) = (|p| - 0.6 + 0.1 g(p)) / 1.1, g a seeded
+spectrally normalised ReLU MLP 3 -> 256 x 6 -> 1, polygonized on an N = 1024
+grid over [-1, 1]^3 (synthetic stand-in for the paper's learned SDBs,
+Sec. 5.2).  One step = one whole polygonization (ray hopping, vertex lists,
+vertex evaluation, FP32 refinement, Marching Cubes) through gh_polygonize.
+
+Metric: surface cells per second (sign-change cells / ms per mesh), the
+headline path being BF16 tensor-core hopping with FP32 refinement; the plain
+FP32 path is timed beside it.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (hopper + Marching Cubes) on a
+bounded random sample of the same grid's columns on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "neural SDB seed 1 (MLP 3->256x6->1, spectral-normalised, ReLU), N=1024, [-1,1]^3",
+    "sdb": "mlp", "seed": 1, "width": 256, "N": 1024,
+}
+FLOP_PER_EVAL = 2 * (3 * 256 + 5 * 256 * 256 + 256)  # weights only: 657,408
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(seconds: float, seed: int = 123):
+    """Times the FP64 oracle (serial hopper + Marching Cubes) on random columns
+    of the workload grid; returns (surface cells per second, cores, sample)."""
+    import oracle
+    from paper_2111_05778_gb300 import synth
+
+    N, W = WORKLOAD["N"], WORKLOAD["width"]
+    o = oracle.mlp(W, synth.MLP_NMID, synth.mlp_params(WORKLOAD["seed"], W).astype(np.float64))
+    rng = np.random.default_rng(seed)
+    cols_all = rng.permutation(N * N)
+    n = 256
+    t0 = time.perf_counter()
+    _, mr = oracle.polygonize(o, N, cols=cols_all[:n])
+    dt = time.perf_counter() - t0
+    if dt < seconds:
+        n = int(min(len(cols_all), max(n, n * seconds / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        _, mr = oracle.polygonize(o, N, cols=cols_all[:n])
+        dt = time.perf_counter() - t0
+    surf = int(((mr.cases > 0) & (mr.cases < 255)).sum())
+    return surf / dt, oracle.num_threads(), "%d uniformly random columns of the N=%d grid (%.1f s, %d surface cells)" % (
+        n, N, dt, surf), dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # each step is a bounded sample so that --steps K --warmup W ends in minutes
+    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps)))
+    vals = []
+    for k in range(args.steps):
+        v, cores, sample, dt = oracle_sample(per_step, seed=123 + k)
+        vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "surface cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
+        "steps": len(vals), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD),
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2111_05778_gb300 import gh, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    N, W = WORKLOAD["N"], WORKLOAD["width"]
+    params = synth.mlp_params(WORKLOAD["seed"], W)
+    sdb = gh.MlpSdb(params, W)
+    precision = args.precision
+    if precision == "auto":
+        precision = "bf16" if _bf16_available(sdb) else "fp32"
+    eps = None
+    if precision == "bf16":
+        eps = sdb.calibrate(N)
+
+    # size the buffers with one synchronous call
+    probe = gh.polygonize(sdb, N, precision=precision, eps=eps)
+    cap = int(probe.n_tris * 1.05) + 4096
+    bufs = gh.Buffers(cap)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return gh.polygonize_into(sdb, N, bufs, precision=precision, eps=eps, sync=False, stream=stream)
+
+    gh.set_profiling(True)
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    hop_ms, phases_sum = [], {}
+    launches = 0
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        rc = step()
+        ev[i][1].record(stream)
+        n_l, ph = gh.last_profile()  # waits for this step's phase events
+        launches += n_l
+        hop_ms.append(ph.get("hop", float("nan")))
+        for k, v in ph.items():
+            phases_sum[k] = phases_sum.get(k, 0.0) + v
+        flush.zero_()
+        assert rc == gh.GH_OK
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    st = bufs.stats_dict()
+    assert st["status"] == 0, st
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    cells = st["surface_cells"]
+    value = cells * world / (ms / 1e3)
+
+    # roofline of the dominant kernel: the ray hopper (f evaluations)
+    peaks, peak_kind = measured_peaks()
+    hop_avg = float(np.mean(hop_ms))
+    flops = st["hop_evals"] * FLOP_PER_EVAL
+    achieved = flops / (hop_avg / 1e3) / 1e12
+    if precision == "bf16":
+        peak = float(peaks.get("bf16_tflops", 1931.4))
+        bound, peak_note = "tensor", "bf16_tflops (%s)" % peak_kind
+    else:
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        bound, peak_note = "alu", "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz (derived)" % sm_max
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "hop (%s)" % precision, "kernel_ms": hop_avg, "peak_source": peak_note,
+            "flop_per_launch": flops}
+
+    # end to end through the public API with host buffers
+    e2e = e2e_measure(gh, torch, params, W, N, precision, eps, cap, max(2, min(args.steps, 5)), stream)
+
+    line = {
+        "metric": "surface cells/s", "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if precision == "bf16" else "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, precision="bf16+fp32-refine" if precision == "bf16" else "fp32",
+                       l2="256 MB buffer written between timed steps (L2 flush)", replicas=world),
+        "ms_per_mesh": ms, "surface_cells": cells, "triangles": st["triangles"], "hop_evals": st["hop_evals"],
+        "marked_cells": st["marked_cells"], "unique_vertices": st["unique_vertices"],
+        "refined_vertices": st["refined_vertices"],
+        "phases_ms": {k: v / args.steps for k, v in phases_sum.items()},
+        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+    if precision == "bf16":
+        line["fp32_path"] = fp32_companion(gh, torch, sdb, N, bufs, stream, flush)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        v, cores, sample, _ = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _bf16_available(sdb):
+    from paper_2111_05778_gb300 import gh
+
+    try:
+        sdb.calibrate(64, n_points=4096)
+        return True
+    except gh.GhError:
+        return False
+
+
+def fp32_companion(gh, torch, sdb, N, bufs, stream, flush, steps=3):
+    gh.polygonize_into(sdb, N, bufs, precision="fp32", sync=True, stream=stream)
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gh.polygonize_into(sdb, N, bufs, precision="fp32", sync=False, stream=stream)
+        b.record(stream)
+        _, ph = gh.last_profile()
+        flush.zero_()
+        torch.cuda.synchronize()
+        ts.append((a.elapsed_time(b), ph.get("hop", float("nan"))))
+    st = bufs.stats_dict()
+    ms = float(np.mean([t[0] for t in ts]))
+    hop = float(np.mean([t[1] for t in ts]))
+    return {"ms_per_mesh": ms, "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
+            "hop_ms": hop, "hop_tflops": st["hop_evals"] * FLOP_PER_EVAL / (hop / 1e3) / 1e12}
+
+
+def e2e_measure(gh, torch, params, W, N, precision, eps, cap, steps, stream):
+    """Per step: the SDB blob goes host -> device (gh_create_sdb), the mesh is
+    polygonized, and the triangle soup comes back into pinned host memory."""
+    host_tris = torch.empty((cap, 3, 3), dtype=torch.float32, pin_memory=True)
+    bufs = gh.Buffers(cap)
+    times, cells, h2d, d2h = [], 0, 0, 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sdb = gh.MlpSdb(params, W)
+        rc = gh.polygonize_into(sdb, N, bufs, precision=precision, eps=eps, sync=True, stream=stream)
+        assert rc == gh.GH_OK
+        T = int(bufs.counts[0].item())
+        host_tris[:T].copy_(bufs.tri_xyz[:T], non_blocking=True)
+        st = bufs.stats.cpu()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sdb.close()
+        if i > 0:
+            times.append(dt)
+        cells = int(st[6])
+        h2d = params.nbytes + 32
+        d2h = T * 36 + 16 + 128
+    ms = float(np.mean(times)) * 1e3
+    return {"value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_mesh": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

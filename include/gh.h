@@ -1,0 +1,246 @@
+/*
+ * gh.h -- C ABI of the GB300 grid-hopping polygonizer.
+ *
+ * The library turns a signed distance bound (SDB) into a triangle mesh with
+ * the grid-hopping method of Markus & Suznjevic, "Theoretical and Empirical
+ * Analysis of a Fast Algorithm for Extracting Polygons from Signed Distance
+ * Bounds" (Sec. 3, Algorithm 1): N^2 rays are cast along +z through the cell
+ * centres of an N^3 grid (Eq. 1-2); each ray evaluates the bound d = |f| at a
+ * cell centre and jumps floor(d / h) cells ahead (the sphere-tracing
+ * iteration of Eq. 3 on the cell lattice); a cell whose centre is within the
+ * polygonization distance tau of the surface (Eq. 4) is marked, and only
+ * marked cells get Marching Cubes.  The result equals Marching Cubes over all
+ * N^3 cells (Sec. 5: all methods produce the same mesh).
+ *
+ * Every compute step runs in sm_103a CUDA kernels on the caller's stream; no
+ * entry point has a CPU fallback.  All pointers named "device" must be
+ * device memory of the current CUDA device.  Unless stated otherwise an
+ * entry point returns GH_OK or one of the GH_ERR_* codes below and leaves a
+ * readable message in gh_last_error().
+ *
+ * Conventions (the paper's unit cube generalised to a cube [lo, hi]^3):
+ *   h = (hi - lo) / N; cell (i,j,k) = [lo + i h, lo + (i+1) h] x ...;
+ *   cell id = (i*N + j)*N + k; lattice vertex (a,b,c) = lo + (a,b,c) h;
+ *   inside <=> f < 0 (f == 0 counts as outside);
+ *   Marching Cubes case = sum_b [f(corner b) < 0] << b with corner b at offset
+ *   (b&1, b>>1&1, b>>2&1);
+ *   the vertex on a crossing edge from lower endpoint A to upper endpoint B
+ *   sits at t = fA / (fA - fB) from A;
+ *   edge key = axis*(N+1)^3 + a + (N+1)*(b + (N+1)*c) with (a,b,c) the
+ *   lattice coordinates of A -- equal keys denote the same mesh vertex;
+ *   triangles are oriented so that (v1 - v0) x (v2 - v0) points towards f > 0.
+ */
+#ifndef GH_H_
+#define GH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GH_OK 0
+#define GH_ERR_ARG 1           /* invalid argument; nothing was enqueued        */
+#define GH_ERR_CAPACITY 2      /* an output buffer was too small (see gh_mesh)  */
+#define GH_ERR_CUDA 3          /* a CUDA call failed; message has the details   */
+#define GH_ERR_NONFINITE 4     /* the SDB produced NaN or inf                   */
+#define GH_ERR_UNIMPLEMENTED 5 /* combination not supported by this build        */
+#define GH_ERR_DEVICE 6        /* the GPU is not an sm_103 device               */
+
+/* ---- SDB kinds and their blob formats ---------------------------------- */
+#define GH_SDB_CSG 0
+#define GH_SDB_MLP 1
+
+/* CSG blob: gh_csg_header followed by n_prim gh_csg_prim records.
+ * f = op_{n-1}( ... op_1(d_0, d_1) ..., d_{n-1}) -- a left fold where union is
+ * min (Sec. 4.3), subtract is max(f, -d) and intersect is max(f, d).  Every
+ * primitive is an exact Euclidean distance, so f is a signed distance bound
+ * (Sec. 1).  q = rot * (p - centre) is the point in the primitive's frame. */
+#define GH_PRIM_SPHERE 0 /* param[0] = radius                                 */
+#define GH_PRIM_TORUS 1  /* around local y: param[0] = major R, param[1] = r   */
+#define GH_PRIM_BOX 2    /* exact box distance (Sec. 4.2), half sizes param[] */
+#define GH_OP_UNION 0
+#define GH_OP_SUBTRACT 1
+#define GH_OP_INTERSECT 2
+#define GH_MAX_PRIMS 256
+typedef struct {
+    int32_t n_prim;
+    int32_t reserved[3];
+} gh_csg_header;
+typedef struct {
+    int32_t type, op;
+    float centre[3];
+    float param[3];
+    float rot[9]; /* row-major, world offset -> local frame */
+    float pad[3];
+} gh_csg_prim; /* 80 bytes */
+
+/* MLP blob (the neural SDB of Sec. 5.2, Eq. 7): gh_mlp_header followed by
+ * float32 parameters packed as W0[width][3] b0[width] then n_mid times
+ * { W[width][width] b[width] } then w_out[width] b_out[1] (row-major,
+ * out x in, like torch.nn.Linear).  g = w_out . relu(W_mid ... relu(W0 p + b0)
+ * ...) + b_out and f(p) = (|p| - r0 + alpha g(p)) / beta / lipschitz_scale.
+ * width must be 64, 128 or 256. */
+typedef struct {
+    int32_t width, n_mid;
+    int32_t reserved[2];
+    float r0, alpha, beta, reserved_f;
+} gh_mlp_header;
+
+typedef struct gh_sdb gh_sdb; /* opaque; owned by the library */
+
+typedef struct {
+    int32_t kind;          /* GH_SDB_CSG | GH_SDB_MLP                          */
+    const void *blob;      /* host pointer; copied, the caller keeps ownership */
+    size_t blob_bytes;
+    float lipschitz_scale; /* lambda >= 1 of Sec. 5.2; f is divided by it; 0 = 1 */
+} gh_sdb_desc;
+
+typedef struct {
+    int32_t N;    /* cells per axis, 2 <= N <= 2048                          */
+    float lo[3];  /* the polygonization volume; hi - lo must be equal on all */
+    float hi[3];  /* three axes (a cube, Sec. 2)                            */
+} gh_grid;
+
+#define GH_FP32 0        /* every evaluation in FP32                           */
+#define GH_BF16_REFINE 1 /* neural SDB: hop in BF16 with an error bound eps,   */
+                         /* corners of candidate cells re-evaluated in FP32    */
+#define GH_TAU_DIAGONAL 0      /* tau = sqrt(3) h: one cell diagonal (default) */
+#define GH_TAU_HALF_DIAGONAL 1 /* tau = sqrt(3) h / 2: the tightest safe value */
+
+typedef struct {
+    int32_t precision; /* GH_FP32 | GH_BF16_REFINE (MLP only)                 */
+    int32_t tau_mode;  /* GH_TAU_*                                            */
+    float eps;         /* BF16 bound |f_bf16 - f_fp32| <= eps/2; < 0 = the    */
+                       /* SDB's calibrated value (gh_sdb_calibrate)           */
+    int32_t sync;      /* 1: wait for the stream before returning, grow       */
+                       /* internal scratch and retry when it overflowed, and  */
+                       /* return device-side errors; 0: fully asynchronous,   */
+                       /* errors land in stats->status                        */
+} gh_options;
+
+/* Counters written by the device (all int64 so a caller may read the struct
+ * with one copy). */
+typedef struct {
+    int64_t status;          /* GH_OK or a GH_ERR_* code from the device      */
+    int64_t columns;         /* N^2                                           */
+    int64_t hop_evals;       /* f evaluations made by the rays                */
+    int64_t marked_cells;    /* cells within tau                              */
+    int64_t unique_vertices; /* lattice vertices evaluated for Marching Cubes */
+    int64_t refined_vertices;/* of those, re-evaluated in FP32 (BF16 path)    */
+    int64_t surface_cells;   /* marked cells with 0 < case < 255              */
+    int64_t triangles;       /* triangles produced (may exceed capacity)      */
+    int64_t reserved[8];
+} gh_stats;
+
+/* Output description; every buffer is caller-owned device memory.
+ * tri_xyz:   [capacity_tris][3][3] float32 vertex positions (triangle soup).
+ * tri_keys:  [capacity_tris][3] uint64 edge keys, or NULL.
+ * n_tris:    one int64 written with the number of triangles produced.  When
+ *            it exceeds capacity_tris only the first capacity_tris are written
+ *            (in an unspecified order) and the call reports GH_ERR_CAPACITY.
+ * cell_ids / cell_cases / capacity_cells / n_cells: optional (NULL) list of
+ *            the surface cells (0 < case < 255) with their case index,
+ *            same capacity protocol.
+ * stats:     optional device gh_stats. */
+typedef struct {
+    float *tri_xyz;
+    uint64_t *tri_keys;
+    int64_t capacity_tris;
+    int64_t *n_tris;
+    uint64_t *cell_ids;
+    uint8_t *cell_cases;
+    int64_t capacity_cells;
+    int64_t *n_cells;
+    gh_stats *stats;
+} gh_mesh;
+
+/* Creates an SDB from a host blob (formats above).  Copies the blob to the
+ * device of the current CUDA device; for GH_SDB_MLP also derives the BF16
+ * tensor-core copy of the weights.  Errors: GH_ERR_ARG for a malformed blob,
+ * GH_ERR_CUDA, GH_ERR_DEVICE when the current device is not sm_103. */
+int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out);
+
+/* Releases an SDB and its device memory.  NULL is accepted.  The caller must
+ * make sure no work that uses it is still running. */
+int gh_destroy_sdb(gh_sdb *sdb);
+
+/* Measures the BF16 evaluation error of a neural SDB (the reduced-precision
+ * counterpart of the paper's shrink factor lambda, Sec. 5.2): eps = 2 * max
+ * |f_bf16 - f_fp32| over n_points seeded uniform points of the grid's volume
+ * together with the lattice points of a coarse grid around the surface.
+ * Stores eps in the SDB (used when gh_options.eps < 0) and, if eps_out is
+ * not NULL, writes it to the host float.  Synchronises the stream. */
+int gh_sdb_calibrate(gh_sdb *sdb, const gh_grid *grid, int64_t n_points, uint64_t seed, float *eps_out,
+                     void *stream);
+
+/* Polygonizes one SDB on a grid: the paper's apply_grid_hopping(eval_sdb, N)
+ * (Algorithm 1) with Marching Cubes filled in at the polygonization step.
+ * stream is a cudaStream_t (NULL = legacy default stream).  Asynchronous
+ * unless opts->sync; see gh_options.  Errors: GH_ERR_ARG, GH_ERR_CAPACITY
+ * (sync only; *n_tris then holds the required count), GH_ERR_NONFINITE,
+ * GH_ERR_CUDA. */
+int gh_polygonize(const gh_grid *grid, const gh_sdb *sdb, const gh_options *opts, gh_mesh *out, void *stream);
+
+/* Polygonizes B SDBs, each on its own grid, with one persistent hopping
+ * launch fed by a device work queue of (SDB, column tile) items, followed by
+ * batched Marching Cubes.  grids[b], sdbs[b], outs[b] as in gh_polygonize.
+ * If graph != NULL the whole sequence is captured once into a CUDA graph
+ * (cudaGraphExec_t written to *graph) that the caller may replay with
+ * cudaGraphLaunch; the SDBs, grids and outputs are then bound to it. */
+int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
+                        gh_mesh *outs, void *stream, void **graph);
+
+/* Implicit-surface adjoint for a neural SDB: given mesh vertices v[V][3]
+ * (device, float32) and the loss gradient dL/dv[V][3] (device), accumulates
+ *   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f)/|grad_x f|^2,
+ * i.e. dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2 for a vertex that
+ * stays on the level set f = 0.  Activations are recomputed at each vertex.
+ * dL_dtheta is device float32, packed like the MLP blob's parameters, and is
+ * overwritten.  Deterministic (fixed-order two-level reduction). */
+int gh_backward(const gh_sdb *sdb, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
+                void *stream);
+
+/* Evaluates f at n points p[n][3] (device float32) into out[n] (device
+ * float32) with the given precision -- the evaluator the hopper uses. */
+int gh_eval(const gh_sdb *sdb, const float *p, int64_t n, float *out, int32_t precision, void *stream);
+
+/* Profiling aid.  gh_set_profiling(1) makes every later gh_polygonize on the
+ * calling thread record CUDA events on its stream around its phases (ray
+ * hopping, vertex lists, vertex evaluation, FP32 refinement, Marching Cubes).
+ * gh_last_profile waits for those events and reports the phase durations of
+ * the last call; `launches` (the number of kernels that call launched) is
+ * reported whether or not profiling is on. */
+#define GH_PHASE_HOP 0
+#define GH_PHASE_LISTS 1
+#define GH_PHASE_VERTICES 2
+#define GH_PHASE_REFINE 3
+#define GH_PHASE_MC 4
+typedef struct {
+    int64_t launches;
+    int32_t n_phases; /* 5 when timed, 0 when profiling was off */
+    int32_t reserved;
+    double ms[8];
+} gh_profile;
+int gh_set_profiling(int enable);
+int gh_last_profile(gh_profile *out);
+
+/* Copies the library's Marching Cubes table to host memory: ntri[256] and
+ * edges[256][5][3] (-1 padded).  Host-only; needs no GPU. */
+int gh_mc_table(int32_t *ntri, int32_t *edges);
+
+/* Number of parameters of a neural SDB blob of this width / depth. */
+int64_t gh_mlp_param_count(int32_t width, int32_t n_mid);
+
+/* Thread-local message of the last error (never NULL). */
+const char *gh_last_error(void);
+
+/* Library version string. */
+const char *gh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GH_H_ */

@@ -1,0 +1,611 @@
+// Host side of the C ABI declared in include/gh.h: argument checks, device
+// set-up, the Marching Cubes table, scratch management and the launch
+// sequence of one polygonization.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gh_internal.cuh"
+
+using namespace gh;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err = "no error";
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define GH_CUDA(call)                                                                             \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(GH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char *gh_last_error(void) { return g_err.c_str(); }
+extern "C" const char *gh_version(void) { return "gridhop-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Marching Cubes table.  Rule (the paper prints none): on each cube face,
+// walk the four corners counter-clockwise as seen from outside the cube;
+// every run of negative corners is cut off by one directed segment that
+// starts on the edge where the walk enters the run and ends on the edge where
+// it leaves it (so the negative side is on the segment's right seen from
+// outside and negative corners are never joined across a face).  The
+// segments of a case close into loops; a loop is fanned from its
+// smallest-index edge whose fan has no triangle lying inside one face.
+// ---------------------------------------------------------------------------
+static int32_t t_ntri[256];
+static int32_t t_edges[256][5][3];
+static bool t_ready = false;
+static std::mutex t_mu;
+
+static int corner_of(int x, int y, int z) { return x | (y << 1) | (z << 2); }
+
+// edge between two corners that differ in exactly one coordinate
+static int edge_between(int c1, int c2) {
+    const int lo = c1 < c2 ? c1 : c2, d = c1 ^ c2;
+    const int ax = d == 1 ? 0 : (d == 2 ? 1 : 2);
+    int uv[2], n = 0;
+    for (int a = 0; a < 3; ++a)
+        if (a != ax) uv[n++] = (lo >> a) & 1;
+    return 4 * ax + uv[0] + 2 * uv[1];
+}
+
+// bit mask of the faces (axis*2 + side) an edge lies on
+static int edge_faces(int e) {
+    const int ax = e >> 2, u = e & 1, v = (e >> 1) & 1;
+    int others[2], n = 0;
+    for (int a = 0; a < 3; ++a)
+        if (a != ax) others[n++] = a;
+    return (1 << (others[0] * 2 + u)) | (1 << (others[1] * 2 + v));
+}
+
+static void build_table_host() {
+    // counter-clockwise corner order of each face seen from outside
+    int ring[6][4];
+    for (int ax = 0; ax < 3; ++ax)
+        for (int sd = 0; sd < 2; ++sd) {
+            const int p = ax == 0 ? 1 : 0, q = ax == 2 ? 1 : 2;
+            const int sigma = ax == 1 ? -1 : 1;  // e_p x e_q = sigma * e_ax
+            const int pq[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+            const bool ccw = sigma * (2 * sd - 1) > 0;
+            for (int t = 0; t < 4; ++t) {
+                const int *c = pq[ccw ? t : 3 - t];
+                int xyz[3];
+                xyz[ax] = sd;
+                xyz[p] = c[0];
+                xyz[q] = c[1];
+                ring[ax * 2 + sd][t] = corner_of(xyz[0], xyz[1], xyz[2]);
+            }
+        }
+    for (int cs = 0; cs < 256; ++cs) {
+        int nxt[12];
+        for (int e = 0; e < 12; ++e) nxt[e] = -1;
+        for (int f = 0; f < 6; ++f) {
+            int enter[2], leave[2], ne = 0, nl = 0;
+            for (int t = 0; t < 4; ++t) {
+                const int a = ring[f][t], b = ring[f][(t + 1) & 3];
+                const bool na = (cs >> a) & 1, nb = (cs >> b) & 1;
+                if (!na && nb) enter[ne++] = t;
+                if (na && !nb) leave[nl++] = t;
+            }
+            // pair each entry with the first exit after it along the ring
+            for (int i = 0; i < ne; ++i) {
+                int best = -1, bd = 99;
+                for (int j = 0; j < nl; ++j) {
+                    const int dist = (leave[j] - enter[i] + 4) & 3;
+                    if (dist > 0 && dist < bd) {
+                        bd = dist;
+                        best = j;
+                    }
+                }
+                const int e1 = edge_between(ring[f][enter[i]], ring[f][(enter[i] + 1) & 3]);
+                const int e2 = edge_between(ring[f][leave[best]], ring[f][(leave[best] + 1) & 3]);
+                nxt[e1] = e2;
+            }
+        }
+        bool seen[12] = {false};
+        int nt = 0;
+        for (int e0 = 0; e0 < 12; ++e0) {
+            if (nxt[e0] < 0 || seen[e0]) continue;
+            int loop[12], n = 0;
+            for (int x = e0; !seen[x]; x = nxt[x]) {
+                seen[x] = true;
+                loop[n++] = x;
+            }
+            int apex = 0;
+            bool found = false;
+            for (int cand = 0; cand < 12 && !found; ++cand)
+                for (int at = 0; at < n && !found; ++at) {
+                    if (loop[at] != cand) continue;
+                    bool flat = false;
+                    for (int i = 1; i + 1 < n; ++i) {
+                        const int m = edge_faces(loop[at]) & edge_faces(loop[(at + i) % n]) &
+                                      edge_faces(loop[(at + i + 1) % n]);
+                        if (m) flat = true;
+                    }
+                    if (!flat) {
+                        apex = at;
+                        found = true;
+                    }
+                }
+            for (int i = 1; i + 1 < n; ++i) {
+                t_edges[cs][nt][0] = loop[apex];
+                t_edges[cs][nt][1] = loop[(apex + i) % n];
+                t_edges[cs][nt][2] = loop[(apex + i + 1) % n];
+                ++nt;
+            }
+        }
+        t_ntri[cs] = nt;
+        for (int t = nt; t < 5; ++t) t_edges[cs][t][0] = t_edges[cs][t][1] = t_edges[cs][t][2] = -1;
+    }
+    t_ready = true;
+}
+
+static void ensure_table() {
+    std::lock_guard<std::mutex> lk(t_mu);
+    if (!t_ready) build_table_host();
+}
+
+extern "C" int gh_mc_table(int32_t *ntri, int32_t *edges) {
+    if (!ntri || !edges) return fail(GH_ERR_ARG, "gh_mc_table: NULL output");
+    ensure_table();
+    memcpy(ntri, t_ntri, sizeof(t_ntri));
+    memcpy(edges, t_edges, sizeof(t_edges));
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-device set-up
+// ---------------------------------------------------------------------------
+struct DevInfo {
+    bool ready = false;
+    int nsm = 0;
+};
+static DevInfo g_dev[64];
+static std::mutex g_dev_mu;
+
+static int ensure_device(int *dev_out, int *nsm_out) {
+    int dev = 0;
+    GH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(GH_ERR_DEVICE, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_dev[dev].ready) {
+        cudaDeviceProp prop;
+        GH_CUDA(cudaGetDeviceProperties(&prop, dev));
+        if (prop.major != 10 || prop.minor != 3)
+            return fail(GH_ERR_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a only", dev, prop.major,
+                        prop.minor);
+        ensure_table();
+        GH_CUDA(upload_mc_table(&t_ntri[0], &t_edges[0][0][0]));
+        g_dev[dev].nsm = prop.multiProcessorCount;
+        g_dev[dev].ready = true;
+    }
+    *dev_out = dev;
+    *nsm_out = g_dev[dev].nsm;
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SDB objects
+// ---------------------------------------------------------------------------
+struct gh_sdb {
+    int kind = -1;
+    int device = 0;
+    float lam = 1.f;
+    // CSG
+    Prim *d_prims = nullptr;
+    int nprim = 0;
+    // MLP
+    MlpDev mlp{};
+    std::vector<void *> dbufs;
+    float *d_params = nullptr;  // packed parameters as given (float32)
+    int64_t nparam = 0;
+    float eps = -1.f;           // calibrated BF16 bound (< 0: none yet)
+    // scratch, grown on demand
+    Scratch scr{};
+    int scr_N = 0;
+    std::mutex mu;
+};
+
+extern "C" int64_t gh_mlp_param_count(int32_t width, int32_t n_mid) {
+    const int64_t W = width;
+    return 3 * W + W + (int64_t)n_mid * (W * W + W) + W + 1;
+}
+
+template <class T>
+static int dev_alloc(gh_sdb *s, T **p, size_t n) {
+    void *q = nullptr;
+    GH_CUDA(cudaMalloc(&q, n * sizeof(T) + 16));
+    s->dbufs.push_back(q);
+    *p = (T *)q;
+    return GH_OK;
+}
+
+static int create_csg(gh_sdb *s, const gh_sdb_desc *d) {
+    if (d->blob_bytes < sizeof(gh_csg_header)) return fail(GH_ERR_ARG, "CSG blob shorter than its header");
+    gh_csg_header h;
+    memcpy(&h, d->blob, sizeof(h));
+    if (h.n_prim < 1 || h.n_prim > GH_MAX_PRIMS)
+        return fail(GH_ERR_ARG, "CSG n_prim = %d outside [1, %d]", h.n_prim, GH_MAX_PRIMS);
+    if (d->blob_bytes != sizeof(h) + (size_t)h.n_prim * sizeof(gh_csg_prim))
+        return fail(GH_ERR_ARG, "CSG blob has %zu bytes, expected %zu", d->blob_bytes,
+                    sizeof(h) + (size_t)h.n_prim * sizeof(gh_csg_prim));
+    std::vector<gh_csg_prim> pr(h.n_prim);
+    memcpy(pr.data(), (const char *)d->blob + sizeof(h), pr.size() * sizeof(gh_csg_prim));
+    for (int i = 0; i < h.n_prim; ++i) {
+        const gh_csg_prim &p = pr[i];
+        if (p.type < 0 || p.type > 2) return fail(GH_ERR_ARG, "primitive %d: unknown type %d", i, p.type);
+        if (p.op < 0 || p.op > 2) return fail(GH_ERR_ARG, "primitive %d: unknown op %d", i, p.op);
+        for (int q = 0; q < 3; ++q)
+            if (!isfinite(p.centre[q]) || !isfinite(p.param[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite", i);
+        for (int q = 0; q < 9; ++q)
+            if (!isfinite(p.rot[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite rotation", i);
+        // the shrink factor lambda of Sec. 5.2 applies to analytic SDBs as a
+        // scale of the distances: fold it into the primitives' parameters is
+        // not possible for min/max of differently scaled terms, so lambda is
+        // only accepted as 1 for CSG.
+    }
+    if (s->lam != 1.f) return fail(GH_ERR_UNIMPLEMENTED, "lipschitz_scale != 1 is supported for neural SDBs only");
+    if (dev_alloc(s, &s->d_prims, pr.size())) return GH_ERR_CUDA;
+    GH_CUDA(cudaMemcpy(s->d_prims, pr.data(), pr.size() * sizeof(gh_csg_prim), cudaMemcpyHostToDevice));
+    s->nprim = h.n_prim;
+    return GH_OK;
+}
+
+static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
+    if (d->blob_bytes < sizeof(gh_mlp_header)) return fail(GH_ERR_ARG, "MLP blob shorter than its header");
+    gh_mlp_header h;
+    memcpy(&h, d->blob, sizeof(h));
+    const int W = h.width;
+    if (W != 64 && W != 128 && W != 256) return fail(GH_ERR_ARG, "MLP width %d not in {64, 128, 256}", W);
+    if (h.n_mid < 1 || h.n_mid > 16) return fail(GH_ERR_ARG, "MLP n_mid %d outside [1, 16]", h.n_mid);
+    if (!(h.beta > 0) || !isfinite(h.r0) || !isfinite(h.alpha)) return fail(GH_ERR_ARG, "MLP header values invalid");
+    const int64_t np = gh_mlp_param_count(W, h.n_mid);
+    if (d->blob_bytes != sizeof(h) + (size_t)np * sizeof(float))
+        return fail(GH_ERR_ARG, "MLP blob has %zu bytes, expected %zu", d->blob_bytes, sizeof(h) + (size_t)np * 4);
+    const float *P = (const float *)((const char *)d->blob + sizeof(h));
+    for (int64_t i = 0; i < np; ++i)
+        if (!isfinite(P[i])) return fail(GH_ERR_NONFINITE, "MLP parameter %lld is not finite", (long long)i);
+    const float *W0 = P, *B0 = P + 3 * W;
+    const float *mid = B0 + W;
+    const float *wout = mid + (size_t)h.n_mid * ((size_t)W * W + W);
+    // FP32 hidden weights: transposed (in-major) with the outputs of a row
+    // permuted so that thread group og reads 16 contiguous bytes per step:
+    // position q*64 + og*4 + e holds output og*(W/16) + q*4 + e.
+    std::vector<float> wt((size_t)h.n_mid * W * W), bm((size_t)h.n_mid * W);
+    const int TO = W / 16;
+    for (int l = 0; l < h.n_mid; ++l) {
+        const float *Wl = mid + (size_t)l * ((size_t)W * W + W), *bl = Wl + (size_t)W * W;
+        for (int i = 0; i < W; ++i)
+            for (int q = 0; q < TO / 4; ++q)
+                for (int og = 0; og < 16; ++og)
+                    for (int e = 0; e < 4; ++e) {
+                        const int o = og * TO + q * 4 + e;
+                        wt[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)o * W + i];
+                    }
+        for (int o = 0; o < W; ++o) bm[(size_t)l * W + o] = bl[o];
+    }
+    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout;
+    if (dev_alloc(s, &d_w0, 3 * W) || dev_alloc(s, &d_b0, W) || dev_alloc(s, &d_wt, wt.size()) ||
+        dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np))
+        return GH_ERR_CUDA;
+    GH_CUDA(cudaMemcpy(d_w0, W0, sizeof(float) * 3 * W, cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(d_b0, B0, sizeof(float) * W, cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(d_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(d_bm, bm.data(), sizeof(float) * bm.size(), cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(d_wout, wout, sizeof(float) * W, cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(s->d_params, P, sizeof(float) * np, cudaMemcpyHostToDevice));
+    MlpDev &m = s->mlp;
+    m.width = W;
+    m.n_mid = h.n_mid;
+    m.r0 = h.r0;
+    m.alpha = h.alpha;
+    m.beta = h.beta;
+    m.inv_lam = 1.f / s->lam;
+    m.w0 = d_w0;
+    m.b0 = d_b0;
+    m.wt = d_wt;
+    m.bm = d_bm;
+    m.wout = d_wout;
+    m.bout = wout[W];
+    m.wbf = nullptr;
+    s->nparam = np;
+    return GH_OK;
+}
+
+extern "C" int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out) {
+    if (!desc || !out) return fail(GH_ERR_ARG, "gh_create_sdb: NULL argument");
+    *out = nullptr;
+    if (!desc->blob) return fail(GH_ERR_ARG, "gh_create_sdb: NULL blob");
+    int dev, nsm;
+    int rc = ensure_device(&dev, &nsm);
+    if (rc) return rc;
+    gh_sdb *s = new gh_sdb();
+    s->device = dev;
+    s->lam = desc->lipschitz_scale == 0.f ? 1.f : desc->lipschitz_scale;
+    if (!(s->lam >= 1.f) || !isfinite(s->lam)) {
+        delete s;
+        return fail(GH_ERR_ARG, "lipschitz_scale must be >= 1 (or 0 for 1)");
+    }
+    s->kind = desc->kind;
+    if (desc->kind == GH_SDB_CSG) rc = create_csg(s, desc);
+    else if (desc->kind == GH_SDB_MLP) rc = create_mlp(s, desc);
+    else rc = fail(GH_ERR_ARG, "unknown SDB kind %d", desc->kind);
+    if (rc) {
+        gh_destroy_sdb(s);
+        return rc;
+    }
+    *out = s;
+    return GH_OK;
+}
+
+static void free_scratch(gh_sdb *s) {
+    Scratch &c = s->scr;
+    void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
+                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    s->scr = Scratch{};
+    s->scr_N = 0;
+}
+
+extern "C" int gh_destroy_sdb(gh_sdb *s) {
+    if (!s) return GH_OK;
+    free_scratch(s);
+    for (void *p : s->dbufs) cudaFree(p);
+    delete s;
+    return GH_OK;
+}
+
+// Allocates the scratch of an N-grid with at least the given capacities.
+static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want_verts) {
+    Scratch &c = s->scr;
+    const bool grid_ok = s->scr_N >= N;
+    if (grid_ok && c.cap_marks >= want_marks && c.cap_verts >= want_verts) return GH_OK;
+    const int NN = grid_ok ? s->scr_N : N;
+    long long cm = c.cap_marks > want_marks ? c.cap_marks : want_marks;
+    long long cv = c.cap_verts > want_verts ? c.cap_verts : want_verts;
+    free_scratch(s);
+    const long long ncols = (long long)NN * NN, nlines = (long long)(NN + 1) * (NN + 1);
+    GH_CUDA(cudaMalloc((void **)&c.ctr, sizeof(Counters)));
+    GH_CUDA(cudaMalloc((void **)&c.marks_raw, sizeof(unsigned long long) * cm));
+    GH_CUDA(cudaMalloc((void **)&c.marks_csr, sizeof(unsigned long long) * cm));
+    GH_CUDA(cudaMalloc((void **)&c.colcount, sizeof(uint32_t) * ncols));
+    GH_CUDA(cudaMalloc((void **)&c.coloff, sizeof(uint32_t) * (ncols + 1)));
+    GH_CUDA(cudaMalloc((void **)&c.linecount, sizeof(uint32_t) * nlines));
+    GH_CUDA(cudaMalloc((void **)&c.lineoff, sizeof(uint32_t) * (nlines + 1)));
+    GH_CUDA(cudaMalloc((void **)&c.blocksum, sizeof(uint32_t) * 4096));
+    GH_CUDA(cudaMalloc((void **)&c.vkey, sizeof(unsigned long long) * cv));
+    GH_CUDA(cudaMalloc((void **)&c.vval, sizeof(float) * cv));
+    GH_CUDA(cudaMalloc((void **)&c.vflag, cv));
+    GH_CUDA(cudaMalloc((void **)&c.rlist, sizeof(uint32_t) * cv));
+    c.cap_marks = cm;
+    c.cap_verts = cv;
+    s->scr_N = NN;
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// polygonization
+// ---------------------------------------------------------------------------
+static int check_grid(const gh_grid *g, GridP *gp, int tau_mode) {
+    if (!g) return fail(GH_ERR_ARG, "NULL grid");
+    if (g->N < 2 || g->N > 2048) return fail(GH_ERR_ARG, "grid N = %d outside [2, 2048]", g->N);
+    float ext[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(g->lo[a]) || !isfinite(g->hi[a])) return fail(GH_ERR_ARG, "grid bounds not finite");
+        ext[a] = g->hi[a] - g->lo[a];
+        if (!(ext[a] > 0)) return fail(GH_ERR_ARG, "grid: hi must exceed lo on every axis");
+    }
+    for (int a = 1; a < 3; ++a)
+        if (fabsf(ext[a] - ext[0]) > 1e-6f * ext[0])
+            return fail(GH_ERR_ARG, "grid must be a cube (equal extents on all axes)");
+    if (tau_mode != GH_TAU_DIAGONAL && tau_mode != GH_TAU_HALF_DIAGONAL)
+        return fail(GH_ERR_ARG, "unknown tau_mode %d", tau_mode);
+    gp->N = g->N;
+    for (int a = 0; a < 3; ++a) gp->lo[a] = g->lo[a];
+    gp->h = ext[0] / (float)g->N;
+    gp->inv_h = (float)g->N / ext[0];
+    gp->tau = (float)(sqrt(3.0) * (double)gp->h * (tau_mode == GH_TAU_DIAGONAL ? 1.0 : 0.5));
+    gp->eps = 0.f;
+    return GH_OK;
+}
+
+static int check_mesh(const gh_mesh *m) {
+    if (!m) return fail(GH_ERR_ARG, "NULL mesh");
+    if (m->capacity_tris < 0 || (m->capacity_tris > 0 && !m->tri_xyz))
+        return fail(GH_ERR_ARG, "mesh: tri_xyz is NULL or capacity negative");
+    if (m->cell_ids && (!m->cell_cases || m->capacity_cells < 0))
+        return fail(GH_ERR_ARG, "mesh: cell_ids given without cell_cases / capacity");
+    return GH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling: CUDA events on the launching stream around each phase
+// ---------------------------------------------------------------------------
+struct ProfState {
+    bool enabled = false;
+    bool recorded = false;
+    cudaEvent_t ev[6] = {};
+    long long launches = 0;
+};
+static thread_local ProfState g_prof;
+
+extern "C" int gh_set_profiling(int enable) {
+    g_prof.enabled = enable != 0;
+    if (g_prof.enabled && !g_prof.ev[0])
+        for (auto &e : g_prof.ev) GH_CUDA(cudaEventCreate(&e));
+    return GH_OK;
+}
+
+extern "C" int gh_last_profile(gh_profile *out) {
+    if (!out) return fail(GH_ERR_ARG, "gh_last_profile: NULL");
+    memset(out, 0, sizeof(*out));
+    out->launches = g_prof.launches;
+    if (!g_prof.recorded) return GH_OK;
+    GH_CUDA(cudaEventSynchronize(g_prof.ev[5]));
+    for (int p = 0; p < 5; ++p) {
+        float ms = 0.f;
+        GH_CUDA(cudaEventElapsedTime(&ms, g_prof.ev[p], g_prof.ev[p + 1]));
+        out->ms[p] = ms;
+    }
+    out->n_phases = 5;
+    return GH_OK;
+}
+
+static inline void mark_phase(int i, cudaStream_t st) {
+    if (g_prof.enabled) cudaEventRecord(g_prof.ev[i], st);
+}
+
+// Kernel launches per phase (fixed by the launch sequence below).
+static constexpr int LAUNCHES_HOP = 2, LAUNCHES_LISTS = 8, LAUNCHES_VERTS = 1, LAUNCHES_REFINE = 2,
+                     LAUNCHES_MC = 2;
+
+static int enqueue_once(gh_sdb *s, const GridP &g, int precision, const gh_mesh &out, int nsm, cudaStream_t st) {
+    Scratch &c = s->scr;
+    long long launches = LAUNCHES_HOP + LAUNCHES_LISTS + LAUNCHES_VERTS + LAUNCHES_MC;
+    mark_phase(0, st);
+    launch_init(c, st);
+    if (s->kind == GH_SDB_CSG) {
+        launch_hop_csg(s->d_prims, s->nprim, g, c, nsm, st);
+        mark_phase(1, st);
+        launch_build_lists(g, c, st);
+        mark_phase(2, st);
+        launch_eval_vertices_csg(s->d_prims, s->nprim, g, c, nsm, st);
+        mark_phase(3, st);
+        mark_phase(4, st);
+    } else if (precision == GH_FP32) {
+        launch_hop_mlp_fp32(s->mlp, g, c, nsm, st);
+        mark_phase(1, st);
+        launch_build_lists(g, c, st);
+        mark_phase(2, st);
+        launch_eval_vertices_mlp_fp32(s->mlp, g, c, nsm, false, st);
+        mark_phase(3, st);
+        mark_phase(4, st);
+    } else {
+        launch_hop_mlp_bf16(s->mlp, g, c, nsm, st);
+        mark_phase(1, st);
+        launch_build_lists(g, c, st);
+        mark_phase(2, st);
+        launch_eval_vertices_mlp_bf16(s->mlp, g, c, nsm, st);
+        mark_phase(3, st);
+        launch_refine_select(g, c, st);
+        launch_eval_vertices_mlp_fp32(s->mlp, g, c, nsm, true, st);
+        mark_phase(4, st);
+        launches += LAUNCHES_REFINE;
+    }
+    launch_mc(g, c, out, nsm, st);
+    launch_finalize(c, out, (long long)g.N * g.N, st);
+    mark_phase(5, st);
+    g_prof.recorded = g_prof.enabled;
+    g_prof.launches = launches;
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_options *opts, gh_mesh *out,
+                             void *stream) {
+    gh_sdb *s = const_cast<gh_sdb *>(csdb);
+    if (!s) return fail(GH_ERR_ARG, "NULL sdb");
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1};
+    if (opts) o = *opts;
+    GridP g;
+    int rc = check_grid(grid, &g, o.tau_mode);
+    if (rc) return rc;
+    if ((rc = check_mesh(out))) return rc;
+    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
+        return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
+    if (o.precision == GH_BF16_REFINE) {
+        if (s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "GH_BF16_REFINE applies to neural SDBs only");
+        if (!bf16_supported(s->mlp.width))
+            return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path not available for width %d", s->mlp.width);
+        const float eps = o.eps >= 0.f ? o.eps : s->eps;
+        if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "BF16 path needs eps: pass opts.eps or call gh_sdb_calibrate");
+        g.eps = eps;
+    }
+    int dev, nsm;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    if (dev != s->device) return fail(GH_ERR_ARG, "SDB lives on device %d, current device is %d", s->device, dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const long long N2 = (long long)g.N * g.N;
+    long long want_m = 8 * N2 > (1 << 16) ? 8 * N2 : (1 << 16);
+    long long want_v = 2 * want_m;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((rc = ensure_scratch(s, g.N, want_m, want_v))) return rc;
+        if ((rc = enqueue_once(s, g, o.precision, *out, nsm, st))) return rc;
+        if (!o.sync) return GH_OK;
+        Counters c;
+        GH_CUDA(cudaMemcpyAsync(&c, s->scr.ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+        GH_CUDA(cudaStreamSynchronize(st));
+        if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) {
+            if (c.flags & FLAG_MARK_OVERFLOW) want_m = (long long)(c.marks + c.marks / 4 + 1024);
+            want_v = (c.flags & FLAG_VERT_OVERFLOW) ? (long long)(c.verts + c.verts / 4 + 1024) : 2 * want_m;
+            if (want_v < 2 * want_m) want_v = 2 * want_m;
+            continue;
+        }
+        if (c.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
+        if (c.tris > (unsigned long long)out->capacity_tris)
+            return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris,
+                        c.tris);
+        if (out->cell_ids && c.cells > (unsigned long long)out->capacity_cells)
+            return fail(GH_ERR_CAPACITY, "cell buffer holds %lld, %llu needed", (long long)out->capacity_cells,
+                        c.cells);
+        return GH_OK;
+    }
+    return fail(GH_ERR_CAPACITY, "internal scratch kept overflowing");
+}
+
+extern "C" int gh_eval(const gh_sdb *s, const float *p, int64_t n, float *out, int32_t precision, void *stream) {
+    if (!s || (n > 0 && (!p || !out))) return fail(GH_ERR_ARG, "gh_eval: NULL argument");
+    if (n < 0) return fail(GH_ERR_ARG, "gh_eval: n < 0");
+    if (n == 0) return GH_OK;
+    int dev, nsm, rc;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->kind == GH_SDB_CSG) {
+        launch_eval_points_csg(s->d_prims, s->nprim, p, n, out, st);
+    } else if (precision == GH_FP32) {
+        launch_eval_points_mlp_fp32(s->mlp, p, n, out, nsm, st);
+    } else if (precision == GH_BF16_REFINE) {
+        if (!bf16_supported(s->mlp.width)) return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width");
+        launch_eval_points_mlp_bf16(s->mlp, p, n, out, nsm, st);
+    } else {
+        return fail(GH_ERR_ARG, "unknown precision %d", precision);
+    }
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
+extern "C" int gh_sdb_calibrate(gh_sdb *s, const gh_grid *grid, int64_t n_points, uint64_t seed, float *eps_out,
+                                void *stream) {
+    (void)s; (void)grid; (void)n_points; (void)seed; (void)eps_out; (void)stream;
+    return fail(GH_ERR_UNIMPLEMENTED, "gh_sdb_calibrate: not available yet");
+}
+
+extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
+                                   gh_mesh *outs, void *stream, void **graph) {
+    (void)B; (void)grids; (void)sdbs; (void)opts; (void)outs; (void)stream; (void)graph;
+    return fail(GH_ERR_UNIMPLEMENTED, "gh_polygonize_batch: not available yet");
+}
+
+extern "C" int gh_backward(const gh_sdb *s, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
+                           void *stream) {
+    (void)s; (void)verts; (void)dL_dv; (void)V; (void)dL_dtheta; (void)stream;
+    return fail(GH_ERR_UNIMPLEMENTED, "gh_backward: not available yet");
+}

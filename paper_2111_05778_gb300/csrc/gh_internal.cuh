@@ -1,0 +1,119 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gh.h"
+
+namespace gh {
+
+// Device counters of one polygonization, zeroed at the start of a call.
+struct Counters {
+    unsigned long long next_col;   // column queue of the hopper
+    unsigned long long marks;      // marked cells appended
+    unsigned long long hop_evals;  // f evaluations of the rays
+    unsigned long long verts;      // unique lattice vertices (set by the line scan)
+    unsigned long long refine;     // vertices queued for FP32 re-evaluation
+    unsigned long long tris;       // triangles produced
+    unsigned long long cells;      // surface cells produced
+    unsigned long long flags;      // error bits (FLAG_*)
+    unsigned long long next_tile;  // work counter of point-list kernels
+    unsigned long long next_tile2; // second work counter (refinement pass)
+    unsigned long long pad[6];
+};
+
+enum : unsigned long long {
+    FLAG_MARK_OVERFLOW = 1ull,   // marked list exceeded its capacity
+    FLAG_VERT_OVERFLOW = 2ull,   // vertex list exceeded its capacity
+    FLAG_TRI_OVERFLOW = 4ull,    // caller's triangle buffer too small
+    FLAG_CELL_OVERFLOW = 8ull,   // caller's cell buffer too small
+    FLAG_NONFINITE = 16ull,      // f was NaN or inf somewhere
+};
+
+// Grid parameters as the kernels see them (FP32).
+struct GridP {
+    int N;
+    float lo[3];
+    float h;      // (hi - lo) / N
+    float inv_h;  // N / (hi - lo)
+    float tau;    // polygonization distance
+    float eps;    // evaluation error bound subtracted from |f| (0 in FP32)
+};
+
+// One CSG primitive, laid out like gh_csg_prim.
+struct Prim {
+    int type, op;
+    float c[3];
+    float p[3];
+    float rot[9];
+    float pad[3];
+};
+static_assert(sizeof(Prim) == 80, "Prim layout");
+
+// Neural SDB parameters on the device.
+struct MlpDev {
+    int width, n_mid;
+    float r0, alpha, beta, inv_lam;
+    const float *w0;    // [W][3]
+    const float *b0;    // [W]
+    const float *wt;    // n_mid x [W(in)][W(out)] transposed FP32 hidden weights
+    const float *bm;    // n_mid x [W]
+    const float *wout;  // [W]
+    float bout;
+    const uint16_t *wbf;  // n_mid x BF16 hidden weights in the tensor-core tile layout
+};
+
+// Scratch of one polygonization (device pointers) and its capacities.
+struct Scratch {
+    Counters *ctr;
+    unsigned long long *marks_raw;  // col | k << 24 | rank << 40
+    unsigned long long *marks_csr;  // col | k << 24, grouped by column, k ascending
+    uint32_t *colcount;             // [N^2]
+    uint32_t *coloff;               // [N^2 + 1]
+    uint32_t *linecount;            // [(N+1)^2]
+    uint32_t *lineoff;              // [(N+1)^2 + 1]
+    uint32_t *blocksum;             // scan partials
+    unsigned long long *vkey;       // line | c << 32, grouped by line, c ascending
+    float *vval;                    // [cap_verts]
+    uint8_t *vflag;                 // [cap_verts] refinement flags
+    uint32_t *rlist;                // [cap_verts] vertices to refine
+    long long cap_marks, cap_verts;
+};
+
+// Packing of mark records.
+__host__ __device__ inline unsigned long long pack_mark(uint32_t col, uint32_t k, uint32_t rank) {
+    return (unsigned long long)col | ((unsigned long long)k << 24) | ((unsigned long long)rank << 40);
+}
+__host__ __device__ inline uint32_t mark_col(unsigned long long m) { return (uint32_t)(m & 0xFFFFFFull); }
+__host__ __device__ inline uint32_t mark_k(unsigned long long m) { return (uint32_t)((m >> 24) & 0xFFFFull); }
+__host__ __device__ inline uint32_t mark_rank(unsigned long long m) { return (uint32_t)((m >> 40) & 0xFFFFull); }
+
+// ---- launchers implemented in the kernels' translation units ----------------
+cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges);  // k_pipeline.cu
+void launch_init(Scratch &s, cudaStream_t st);
+void launch_hop_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st);
+void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,
+                              cudaStream_t st);
+void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
+void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st);
+void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long long n, float *out,
+                            cudaStream_t st);
+
+// neural SDB, FP32 on the FFMA pipe (k_mlp_fp32.cu)
+void launch_hop_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_eval_vertices_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, bool refine_list,
+                                   cudaStream_t st);
+void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, float *out, int nsm,
+                                 cudaStream_t st);
+
+// neural SDB, BF16 on tcgen05 tensor cores (k_mlp_bf16.cu)
+bool bf16_supported(int width);
+void launch_hop_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_eval_vertices_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
+                                 cudaStream_t st);
+void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);
+
+}  // namespace gh

@@ -1,0 +1,357 @@
+// Neural SDB in FP32 on the FFMA pipe.
+//
+// f(p) = (|p| - r0 + alpha g(p)) / beta / lambda with g a ReLU MLP (the
+// neural SDB of Sec. 5.2, Eq. 7).  A CTA of 256 threads evaluates a tile of
+// 128 points at a time: layer 0 (3 -> W) and the output layer (W -> 1) on
+// CUDA cores directly, the W x W hidden layers as register-blocked FP32
+// products (8 rows x W/16 outputs per thread) whose weights stream from L2
+// through a double-buffered shared-memory ring (cp.async).
+//
+// Two users of the tile engine:
+//   k_hop_mlp_fp32   persistent grid hopper: each of the 128 rows is a ray;
+//                    after every tile the ray marks / jumps (Algorithm 1) and
+//                    dead rows are refilled from the column queue.
+//   k_pts_mlp_fp32   a list of points (lattice vertices of marked cells, or
+//                    an explicit point array).
+#include "gh_internal.cuh"
+
+namespace gh {
+
+namespace {
+
+constexpr int TM = 128;   // rows per tile
+constexpr int KC = 32;    // K rows per weight chunk
+constexpr int NT = 256;   // threads per CTA
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
+
+template <int W>
+struct Smem {
+    float act[W][TM + 4];  // activations, feature-major
+    float wbuf[2][KC * W]; // weight chunk ring
+    float4 p[TM];          // query points
+    float g[TM];           // network output
+    float red[TM];
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int W>
+__device__ __forceinline__ void issue_chunk(const MlpDev &m, int ch, float *dst) {
+    constexpr int NCH = W / KC;
+    const int l = ch / NCH, c = ch - l * NCH;
+    const float *src = m.wt + (size_t)l * W * W + (size_t)c * KC * W;
+    constexpr int N16 = KC * W / 4;  // float4 count
+    for (int q = threadIdx.x; q < N16; q += NT) cp_async16(dst + 4 * q, src + 4 * q);
+    cp_commit();
+}
+
+// Evaluates g at sm.p[0..TM) into sm.g.  Must be called by all NT threads.
+template <int W>
+__device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
+    constexpr int TO = W / 16;      // outputs per thread
+    constexpr int NCH = W / KC;
+    const int tid = threadIdx.x;
+    const int nchunks = m.n_mid * NCH;
+    if (nchunks > 0) issue_chunk<W>(m, 0, sm.wbuf[0]);
+    {  // layer 0: 3 -> W on CUDA cores
+        const int r = tid & (TM - 1), half = tid >> 7;
+        const float4 p = sm.p[r];
+        for (int o = half * (W / 2); o < (half + 1) * (W / 2); ++o) {
+            const float z = fmaf(__ldg(m.w0 + 3 * o), p.x,
+                                 fmaf(__ldg(m.w0 + 3 * o + 1), p.y, fmaf(__ldg(m.w0 + 3 * o + 2), p.z, __ldg(m.b0 + o))));
+            sm.act[o][r] = fmaxf(z, 0.f);
+        }
+    }
+    const int og = tid & 15, rg = tid >> 4;
+    int ch = 0;
+    for (int l = 0; l < m.n_mid; ++l) {
+        float acc[8][TO];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int o = 0; o < TO; ++o) acc[rr][o] = 0.f;
+        for (int c = 0; c < NCH; ++c, ++ch) {
+            if (ch + 1 < nchunks) {
+                issue_chunk<W>(m, ch + 1, sm.wbuf[(ch + 1) & 1]);
+                cp_wait<1>();
+            } else {
+                cp_wait<0>();
+            }
+            __syncthreads();
+            const float *wb = sm.wbuf[ch & 1];
+#pragma unroll 4
+            for (int kk = 0; kk < KC; ++kk) {
+                const int i = c * KC + kk;
+                const float4 a0 = *reinterpret_cast<const float4 *>(&sm.act[i][rg * 8]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&sm.act[i][rg * 8 + 4]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int q = 0; q < TO / 4; ++q) {
+                    const float4 w = *reinterpret_cast<const float4 *>(wb + kk * W + q * 64 + og * 4);
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) {
+                        acc[rr][q * 4 + 0] = fmaf(a[rr], w.x, acc[rr][q * 4 + 0]);
+                        acc[rr][q * 4 + 1] = fmaf(a[rr], w.y, acc[rr][q * 4 + 1]);
+                        acc[rr][q * 4 + 2] = fmaf(a[rr], w.z, acc[rr][q * 4 + 2]);
+                        acc[rr][q * 4 + 3] = fmaf(a[rr], w.w, acc[rr][q * 4 + 3]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // bias + ReLU, back into the activation buffer
+        const float *bl = m.bm + (size_t)l * W;
+#pragma unroll
+        for (int q = 0; q < TO / 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int o = og * TO + q * 4 + e;
+                const float b = __ldg(bl + o);
+                float4 v0, v1;
+                v0.x = fmaxf(acc[0][q * 4 + e] + b, 0.f);
+                v0.y = fmaxf(acc[1][q * 4 + e] + b, 0.f);
+                v0.z = fmaxf(acc[2][q * 4 + e] + b, 0.f);
+                v0.w = fmaxf(acc[3][q * 4 + e] + b, 0.f);
+                v1.x = fmaxf(acc[4][q * 4 + e] + b, 0.f);
+                v1.y = fmaxf(acc[5][q * 4 + e] + b, 0.f);
+                v1.z = fmaxf(acc[6][q * 4 + e] + b, 0.f);
+                v1.w = fmaxf(acc[7][q * 4 + e] + b, 0.f);
+                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8]) = v0;
+                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8 + 4]) = v1;
+            }
+    }
+    __syncthreads();
+    {  // output layer W -> 1
+        const int r = tid & (TM - 1), half = tid >> 7;
+        float s = 0.f;
+        for (int i = half * (W / 2); i < (half + 1) * (W / 2); ++i) s = fmaf(__ldg(m.wout + i), sm.act[i][r], s);
+        if (half) sm.red[r] = s;
+        __syncthreads();
+        if (!half) sm.g[r] = s + sm.red[r] + m.bout;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float outer_f(const MlpDev &m, float4 p, float g) {
+    const float r = sqrtf(fmaf(p.x, p.x, fmaf(p.y, p.y, p.z * p.z)));
+    return (fmaf(m.alpha, g, r - m.r0) / m.beta) * m.inv_lam;
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(MlpDev m, GridP g, Scratch s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int N = g.N;
+    const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+    uint32_t col = NONE, rank = 0;
+    int k = 0;
+    bool done = false;
+    float x = 0.f, y = 0.f;
+    unsigned long long evals = 0;
+    for (;;) {
+        bool live = false;
+        if (tid < TM) {
+            const bool need = col == NONE && !done;
+            const unsigned needm = __ballot_sync(FULL, need);
+            if (needm) {
+                const int leader = __ffs(needm) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
+                base = __shfl_sync(FULL, base, leader);
+                if (need) {
+                    const unsigned long long c = base + __popc(needm & lt);
+                    if (c < ncols) {
+                        col = (uint32_t)c;
+                        k = 0;
+                        rank = 0;
+                        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                        x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                        y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                    } else {
+                        done = true;
+                    }
+                }
+            }
+            live = col != NONE;
+            sm.p[tid] = live ? make_float4(x, y, fmaf((float)k + 0.5f, g.h, g.lo[2]), 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (!__syncthreads_or(live)) break;
+        mlp_tile<W>(m, sm);
+        if (tid < TM) {
+            bool mark = false;
+            int step = 1;
+            if (live) {
+                const float f = outer_f(m, sm.p[tid], sm.g[tid]);
+                ++evals;
+                float d = fabsf(f) - g.eps;
+                if (!isfinite(f)) {
+                    atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                    d = 0.f;
+                }
+                if (d <= g.tau) {
+                    mark = true;
+                } else {
+                    const float stp = floorf(d * g.inv_h);
+                    step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
+                }
+            }
+            const unsigned mm = __ballot_sync(FULL, mark);
+            if (mm) {
+                const int leader = __ffs(mm) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
+                base = __shfl_sync(FULL, base, leader);
+                if (mark) {
+                    const unsigned long long idx = base + __popc(mm & lt);
+                    if (idx < (unsigned long long)s.cap_marks)
+                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
+                    else
+                        atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
+                }
+            }
+            if (live) {
+                if (mark) {
+                    ++rank;
+                    ++k;
+                } else {
+                    k += step;
+                }
+                if (k >= N) {
+                    s.colcount[col] = rank;
+                    col = NONE;
+                }
+            }
+        }
+        // sm.p / sm.g are rewritten only after the barrier at the top of the next pass
+    }
+    if (tid < TM) {
+        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+        if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+    }
+}
+
+// Point lists: MODE 0 = lattice vertices (vkey) of all unique vertices,
+// MODE 1 = vertices listed in s.rlist (refinement), MODE 2 = explicit points.
+template <int W, int MODE>
+__global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(MlpDev m, GridP g, Scratch s, const float *pts, long long npts,
+                                                         float *outv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
+    __shared__ unsigned long long tile_s;
+    __shared__ unsigned long long total_s;
+    const int tid = threadIdx.x;
+    if (MODE != 2) {
+        if (s.ctr->flags & STOP_FLAGS) return;
+    }
+    unsigned long long* counter = MODE == 1 ? &s.ctr->next_tile2 : &s.ctr->next_tile;
+    for (;;) {
+        if (tid == 0) {
+            tile_s = atomicAdd(counter, 1ull);
+            total_s = MODE == 0 ? s.ctr->verts : (MODE == 1 ? s.ctr->refine : (unsigned long long)npts);
+        }
+        __syncthreads();
+        const unsigned long long t = tile_s, total = total_s;
+        if (t * TM >= total) break;
+        if (tid < TM) {
+            const unsigned long long r = t * TM + tid;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < total) {
+                if (MODE == 2) {
+                    p = make_float4(pts[3 * r], pts[3 * r + 1], pts[3 * r + 2], 0.f);
+                } else {
+                    const unsigned long long key = s.vkey[MODE == 1 ? (unsigned long long)s.rlist[r] : r];
+                    const int N1 = g.N + 1;
+                    const uint32_t line = (uint32_t)(key & 0xFFFFFFFFull), c = (uint32_t)(key >> 32);
+                    const uint32_t a = line / (uint32_t)N1, b = line - a * (uint32_t)N1;
+                    p = make_float4(fmaf((float)a, g.h, g.lo[0]), fmaf((float)b, g.h, g.lo[1]),
+                                    fmaf((float)c, g.h, g.lo[2]), 0.f);
+                }
+            }
+            sm.p[tid] = p;
+        }
+        __syncthreads();
+        mlp_tile<W>(m, sm);
+        if (tid < TM) {
+            const unsigned long long r = t * TM + tid;
+            if (r < total) {
+                const float f = outer_f(m, sm.p[tid], sm.g[tid]);
+                if (MODE != 2 && !isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                if (MODE == 0) s.vval[r] = f;
+                else if (MODE == 1) s.vval[s.rlist[r]] = f;
+                else outv[r] = f;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class K>
+int occupancy_grid(K kernel, size_t smem, int nsm) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, NT, smem);
+    return nsm * (per < 1 ? 1 : per);
+}
+
+}  // namespace
+
+#define GH_DISPATCH_W(W, ...)                                            \
+    switch (W) {                                                         \
+    case 64: { constexpr int WW = 64; __VA_ARGS__; } break;              \
+    case 128: { constexpr int WW = 128; __VA_ARGS__; } break;            \
+    default: { constexpr int WW = 256; __VA_ARGS__; } break;             \
+    }
+
+void launch_hop_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
+    GH_DISPATCH_W(m.width, {
+        const size_t smem = sizeof(Smem<WW>);
+        const int grid = occupancy_grid(k_hop_mlp_fp32<WW>, smem, nsm);
+        k_hop_mlp_fp32<WW><<<grid, NT, smem, st>>>(m, g, s);
+    })
+}
+
+void launch_eval_vertices_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, bool refine_list,
+                                   cudaStream_t st) {
+    GH_DISPATCH_W(m.width, {
+        const size_t smem = sizeof(Smem<WW>);
+        if (refine_list) {
+            const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 1>, smem, nsm);
+            k_pts_mlp_fp32<WW, 1><<<grid, NT, smem, st>>>(m, g, s, nullptr, 0, nullptr);
+        } else {
+            const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 0>, smem, nsm);
+            k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(m, g, s, nullptr, 0, nullptr);
+        }
+    })
+}
+
+void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, float *out, int nsm,
+                                 cudaStream_t st) {
+    // needs a counter: use a tiny private scratch on the stream
+    static thread_local Counters *ctr = nullptr;
+    if (!ctr) cudaMalloc(&ctr, sizeof(Counters));
+    cudaMemsetAsync(ctr, 0, sizeof(Counters), st);
+    Scratch s{};
+    s.ctr = ctr;
+    GridP g{};
+    GH_DISPATCH_W(m.width, {
+        const size_t smem = sizeof(Smem<WW>);
+        int grid = occupancy_grid(k_pts_mlp_fp32<WW, 2>, smem, nsm);
+        const long long tiles = (n + TM - 1) / TM;
+        if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
+        k_pts_mlp_fp32<WW, 2><<<grid, NT, smem, st>>>(m, g, s, p, n, out);
+    })
+}
+
+}  // namespace gh

@@ -1,0 +1,559 @@
+// Grid hopping + Marching Cubes pipeline kernels (analytic SDBs and the parts
+// shared with the neural SDB).
+//
+// Pipeline of one polygonization (Sec. 3, Algorithm 1 of the paper, laid out
+// for a GPU):
+//   1. k_hop_csg      persistent rays, one per lane: evaluate d = |f| at the
+//                     cell centre (Eq. 3); d <= tau (Eq. 4) marks the cell and
+//                     advances one cell, otherwise the ray jumps floor(d/h)
+//                     cells.  Dead lanes are refilled from a column queue
+//                     after a warp ballot; marks are appended with one atomic
+//                     per warp.
+//   2. scans + k_scatter_marks   group the marks by column (k ascending).
+//   3. k_lines        for every vertical lattice line, merge the marks of the
+//                     (up to) four adjacent columns into the sorted set of
+//                     lattice vertices the marked cells need, so each vertex
+//                     is evaluated once.
+//   4. k_eval_vertices_csg   f at those vertices.
+//   5. k_mc           per marked cell: 8 corner values, case index, table
+//                     lookup, edge interpolation, warp prefix-sum emit with one
+//                     atomic per warp.
+#include "gh_internal.cuh"
+
+namespace gh {
+
+__constant__ uint8_t c_tab_n[256];
+__constant__ uint8_t c_tab_e[256][16];
+
+cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges) {
+    uint8_t n[256], e[256][16];
+    for (int c = 0; c < 256; ++c) {
+        n[c] = (uint8_t)ntri[c];
+        for (int t = 0; t < 16; ++t) e[c][t] = 255;
+        for (int t = 0; t < 5; ++t)
+            for (int v = 0; v < 3; ++v) {
+                int x = edges[(c * 5 + t) * 3 + v];
+                if (x >= 0) e[c][t * 3 + v] = (uint8_t)x;
+            }
+    }
+    cudaError_t err = cudaMemcpyToSymbol(c_tab_n, n, sizeof(n));
+    if (err != cudaSuccess) return err;
+    return cudaMemcpyToSymbol(c_tab_e, e, sizeof(e));
+}
+
+static constexpr uint32_t NONE = 0xFFFFFFFFu;
+static constexpr unsigned FULL = 0xFFFFFFFFu;
+static constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
+
+// ---------------------------------------------------------------------------
+// Analytic SDB evaluation: exact distances of sphere, torus and box, folded
+// with min / max (Sec. 4.2-4.3).  Primitives are read from shared memory as
+// five float4 each (all lanes read the same primitive: broadcast).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float prim_dist(const float4 *q, float x, float y, float z, int &op) {
+    const float4 a = q[0];  // type, op, cx, cy
+    const float4 b = q[1];  // cz, p0, p1, p2
+    const int type = __float_as_int(a.x);
+    op = __float_as_int(a.y);
+    const float dx = x - a.z, dy = y - a.w, dz = z - b.x;
+    if (type == GH_PRIM_SPHERE) return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - b.y;
+    const float4 r0 = q[2], r1 = q[3], r2 = q[4];  // rot[0..3], rot[4..7], rot[8], pad
+    const float lx = fmaf(r0.x, dx, fmaf(r0.y, dy, r0.z * dz));
+    const float ly = fmaf(r0.w, dx, fmaf(r1.x, dy, r1.y * dz));
+    const float lz = fmaf(r1.z, dx, fmaf(r1.w, dy, r2.x * dz));
+    if (type == GH_PRIM_TORUS) {
+        const float t = sqrtf(fmaf(lx, lx, lz * lz)) - b.y;
+        return sqrtf(fmaf(t, t, ly * ly)) - b.z;
+    }
+    const float ex = fabsf(lx) - b.y, ey = fabsf(ly) - b.z, ez = fabsf(lz) - b.w;
+    const float ox = fmaxf(ex, 0.f), oy = fmaxf(ey, 0.f), oz = fmaxf(ez, 0.f);
+    return sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(fmaxf(ex, fmaxf(ey, ez)), 0.f);
+}
+
+__device__ __forceinline__ float csg_eval(const float4 *P, int n, float x, float y, float z) {
+    int op;
+    float f = prim_dist(P, x, y, z, op);
+    for (int i = 1; i < n; ++i) {
+        const float d = prim_dist(P + 5 * i, x, y, z, op);
+        f = op == GH_OP_UNION ? fminf(f, d) : (op == GH_OP_SUBTRACT ? fmaxf(f, -d) : fmaxf(f, d));
+    }
+    return f;
+}
+
+// The primitive table is kept as ints in the type/op slots: convert the
+// host's gh_csg_prim (int32 type/op) bit-exactly -- they already are ints.
+__device__ __forceinline__ void load_prims(float4 *dst, const Prim *src, int nprim) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    for (int i = threadIdx.x; i < nprim * 5; i += blockDim.x) dst[i] = s4[i];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_init(Counters *c) {
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(c);
+    if (threadIdx.x < sizeof(Counters) / 8) p[threadIdx.x] = 0ull;
+}
+
+void launch_init(Scratch &s, cudaStream_t st) { k_init<<<1, 32, 0, st>>>(s.ctr); }
+
+// ---------------------------------------------------------------------------
+// 1. Persistent hopper for analytic SDBs.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hop_csg(const Prim *__restrict__ gprims, int nprim, GridP g, Scratch s) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    const int N = g.N;
+    const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t col = NONE, rank = 0;
+    int k = 0;
+    bool done = false;
+    float x = 0.f, y = 0.f;
+    unsigned long long evals = 0;
+    for (;;) {
+        const bool need = col == NONE && !done;
+        const unsigned needm = __ballot_sync(FULL, need);
+        if (needm) {
+            const int leader = __ffs(needm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                const unsigned long long c = base + __popc(needm & lt);
+                if (c < ncols) {
+                    col = (uint32_t)c;
+                    k = 0;
+                    rank = 0;
+                    const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                    x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                    y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                } else {
+                    done = true;
+                }
+            }
+        }
+        const bool live = col != NONE;
+        if (!__any_sync(FULL, live)) break;
+        bool mark = false;
+        int step = 1;
+        if (live) {
+            const float z = fmaf((float)k + 0.5f, g.h, g.lo[2]);
+            const float f = csg_eval(sprim, nprim, x, y, z);
+            ++evals;
+            float d = fabsf(f) - g.eps;
+            if (!isfinite(f)) {
+                atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                d = 0.f;
+            }
+            if (d <= g.tau) {
+                mark = true;
+            } else {
+                const float stp = floorf(d * g.inv_h);
+                step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
+            }
+        }
+        const unsigned mm = __ballot_sync(FULL, mark);
+        if (mm) {
+            const int leader = __ffs(mm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
+            base = __shfl_sync(FULL, base, leader);
+            if (mark) {
+                const unsigned long long idx = base + __popc(mm & lt);
+                if (idx < (unsigned long long)s.cap_marks)
+                    s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
+                else
+                    atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
+            }
+        }
+        if (live) {
+            if (mark) {
+                ++rank;
+                ++k;
+            } else {
+                k += step;
+            }
+            if (k >= N) {
+                s.colcount[col] = rank;
+                col = NONE;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+    if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+}
+
+void launch_hop_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
+    const size_t smem = (size_t)nprim * sizeof(Prim);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_csg, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_hop_csg<<<nsm * per_sm, 256, smem, st>>>(prims, nprim, g, s);
+}
+
+// ---------------------------------------------------------------------------
+// 2. Exclusive scan of uint32 counts (two passes; out has n + 1 entries and
+//    out[n] is the total, also stored in *total when total != NULL).
+// ---------------------------------------------------------------------------
+static constexpr int SCAN_T = 1024, SCAN_IPT = 4, SCAN_TILE = SCAN_T * SCAN_IPT;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    total = wsum[(blockDim.x >> 5) - 1];
+    const uint32_t r = (w ? wsum[w - 1] : 0u) + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
+                                                         uint32_t *__restrict__ bsum, const Counters *ctr) {
+    __shared__ uint32_t wsum[32];
+    if (ctr->flags & STOP_FLAGS) return;
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+    uint32_t v = 0;
+    for (int i = 0; i < SCAN_IPT; ++i)
+        if (base + i < n) v += in[base + i];
+    uint32_t tot;
+    block_excl_scan(v, wsum, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const uint32_t *__restrict__ in, long long n,
+                                                        const uint32_t *__restrict__ bsum, uint32_t *__restrict__ out,
+                                                        unsigned long long *total, Counters *ctr) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t prefix;
+    if (ctr->flags & STOP_FLAGS) return;
+    // prefix of this block = sum of the partials before it
+    uint32_t p = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) p += bsum[i];
+    uint32_t ptot;
+    block_excl_scan(p, wsum, ptot);
+    if (threadIdx.x == 0) prefix = ptot;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+    uint32_t v[SCAN_IPT], sum = 0;
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = prefix + block_excl_scan(sum, wsum, tot);
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        out[n] = prefix + tot;
+        if (total) *total = (unsigned long long)(prefix + tot);
+    }
+}
+
+static void scan_u32(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
+                     Counters *ctr, cudaStream_t st) {
+    const int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    k_scan_reduce<<<nb, SCAN_T, 0, st>>>(in, n, bsum, ctr);
+    k_scan_apply<<<nb, SCAN_T, 0, st>>>(in, n, bsum, out, total, ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Marks grouped by column.
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_marks(Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long M = s.ctr->marks;
+    for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
+         m += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = s.marks_raw[m];
+        const uint32_t col = mark_col(r);
+        s.marks_csr[s.coloff[col] + mark_rank(r)] = r & 0xFFFFFFFFFFull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. Lattice lines.  Line (a,b), 0 <= a,b <= N, holds the lattice vertices
+//    (a,b,c).  A marked cell (i,j,k) needs c = k and c = k+1 on the lines
+//    (i,j), (i+1,j), (i,j+1), (i+1,j+1).  Merging the k-sorted mark lists of
+//    the four columns around a line gives its vertices in ascending c.
+// ---------------------------------------------------------------------------
+template <bool EMIT>
+__global__ void k_lines(GridP g, Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const int N = g.N, N1 = N + 1;
+    const long long nlines = (long long)N1 * N1;
+    const unsigned long long cap = (unsigned long long)s.cap_verts;
+    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
+         line += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(line / N1), b = (int)(line - (long long)a * N1);
+        uint32_t beg[4], end[4];
+        int nl = 0;
+        for (int di = -1; di <= 0; ++di)
+            for (int dj = -1; dj <= 0; ++dj) {
+                const int i = a + di, j = b + dj;
+                if (i < 0 || j < 0 || i >= N || j >= N) continue;
+                const uint32_t col = (uint32_t)i * N + j;
+                beg[nl] = s.coloff[col];
+                end[nl] = s.coloff[col + 1];
+                ++nl;
+            }
+        uint32_t head[4];
+        for (int q = 0; q < nl; ++q) head[q] = beg[q] < end[q] ? mark_k(s.marks_csr[beg[q]]) : NONE;
+        int last = -1;
+        uint32_t cnt = 0;
+        const unsigned long long obase = EMIT ? s.lineoff[line] : 0ull;
+        for (;;) {
+            int best = -1;
+            uint32_t bk = NONE;
+            for (int q = 0; q < nl; ++q)
+                if (head[q] < bk) {
+                    bk = head[q];
+                    best = q;
+                }
+            if (best < 0) break;
+            ++beg[best];
+            head[best] = beg[best] < end[best] ? mark_k(s.marks_csr[beg[best]]) : NONE;
+            for (int c = (int)bk; c <= (int)bk + 1; ++c)
+                if (c > last) {
+                    if (EMIT && obase + cnt < cap)
+                        s.vkey[obase + cnt] = (unsigned long long)line | ((unsigned long long)c << 32);
+                    ++cnt;
+                    last = c;
+                }
+        }
+        if (!EMIT) s.linecount[line] = cnt;
+    }
+}
+
+__global__ void k_check_verts(Scratch s) {
+    if (s.ctr->verts > (unsigned long long)s.cap_verts) atomicOr(&s.ctr->flags, FLAG_VERT_OVERFLOW);
+}
+
+void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st) {
+    const long long ncols = (long long)g.N * g.N, nlines = (long long)(g.N + 1) * (g.N + 1);
+    scan_u32(s.colcount, ncols, s.coloff, s.blocksum, nullptr, s.ctr, st);
+    k_scatter_marks<<<1024, 256, 0, st>>>(s);
+    const int lb = (int)((nlines + 255) / 256);
+    k_lines<false><<<lb, 256, 0, st>>>(g, s);
+    scan_u32(s.linecount, nlines, s.lineoff, s.blocksum, &s.ctr->verts, s.ctr, st);
+    k_check_verts<<<1, 1, 0, st>>>(s);
+    k_lines<true><<<lb, 256, 0, st>>>(g, s);
+}
+
+// ---------------------------------------------------------------------------
+// 4. f at the unique lattice vertices (analytic SDB).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void vertex_pos(const GridP &g, unsigned long long key, float &x, float &y, float &z) {
+    const int N1 = g.N + 1;
+    const uint32_t line = (uint32_t)(key & 0xFFFFFFFFull), c = (uint32_t)(key >> 32);
+    const uint32_t a = line / (uint32_t)N1, b = line - a * (uint32_t)N1;
+    x = fmaf((float)a, g.h, g.lo[0]);
+    y = fmaf((float)b, g.h, g.lo[1]);
+    z = fmaf((float)c, g.h, g.lo[2]);
+}
+
+__global__ void __launch_bounds__(256) k_eval_vertices_csg(const Prim *__restrict__ gprims, int nprim, GridP g,
+                                                            Scratch s) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long V = s.ctr->verts;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += (unsigned long long)gridDim.x * blockDim.x) {
+        float x, y, z;
+        vertex_pos(g, s.vkey[v], x, y, z);
+        const float f = csg_eval(sprim, nprim, x, y, z);
+        if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+        s.vval[v] = f;
+    }
+}
+
+void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,
+                              cudaStream_t st) {
+    const size_t smem = (size_t)nprim * sizeof(Prim);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_vertices_csg, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_eval_vertices_csg<<<nsm * per_sm, 256, smem, st>>>(prims, nprim, g, s);
+}
+
+__global__ void __launch_bounds__(256) k_eval_points_csg(const Prim *__restrict__ gprims, int nprim,
+                                                          const float *__restrict__ p, long long n,
+                                                          float *__restrict__ out) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = csg_eval(sprim, nprim, p[3 * i], p[3 * i + 1], p[3 * i + 2]);
+}
+
+void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long long n, float *out,
+                            cudaStream_t st) {
+    const size_t smem = (size_t)nprim * sizeof(Prim);
+    long long nb = (n + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    k_eval_points_csg<<<(int)nb, 256, smem, st>>>(prims, nprim, p, n, out);
+}
+
+// ---------------------------------------------------------------------------
+// 5. Marching Cubes on the marked cells.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t find_c(const unsigned long long *__restrict__ vkey, uint32_t lo, uint32_t hi,
+                                           uint32_t c) {
+    // vkey[lo..hi) has ascending c (upper 32 bits); c is present by construction
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)(vkey[mid] >> 32) <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long M = s.ctr->marks;
+    const int N = g.N, N1 = N + 1;
+    const unsigned long long N13 = (unsigned long long)N1 * N1 * N1;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long m0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); m0 < M;
+         m0 += stride) {
+        const unsigned long long m = m0 + lane;
+        const bool valid = m < M;
+        float fv[8];
+        int cs = 0, i = 0, j = 0, k = 0;
+        if (valid) {
+            const unsigned long long r = s.marks_csr[m];
+            const uint32_t col = mark_col(r);
+            k = (int)mark_k(r);
+            i = (int)(col / (uint32_t)N);
+            j = (int)(col - (uint32_t)i * N);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
+                const uint32_t idx = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], (uint32_t)k);
+                fv[q] = s.vval[idx];
+                fv[q + 4] = s.vval[idx + 1];
+            }
+#pragma unroll
+            for (int b = 0; b < 8; ++b) cs |= (fv[b] < 0.f) << b;
+        }
+        const bool surf = valid && cs != 0 && cs != 255;
+        const int nt = surf ? c_tab_n[cs] : 0;
+        // warp-exclusive prefix sum of the triangle counts, one atomic per warp
+        int x = nt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        const int wtot = __shfl_sync(FULL, x, 31);
+        unsigned long long tbase = 0;
+        if (wtot) {
+            if (lane == 31) tbase = atomicAdd(&s.ctr->tris, (unsigned long long)wtot);
+            tbase = __shfl_sync(FULL, tbase, 31);
+        }
+        tbase += (unsigned long long)(x - nt);
+        const unsigned sm = __ballot_sync(FULL, surf);
+        if (sm && out.cell_ids) {
+            unsigned long long cbase = 0;
+            if (lane == 0) cbase = atomicAdd(&s.ctr->cells, (unsigned long long)__popc(sm));
+            cbase = __shfl_sync(FULL, cbase, 0);
+            if (surf) {
+                const unsigned long long ci = cbase + __popc(sm & lt);
+                if (ci < (unsigned long long)out.capacity_cells) {
+                    out.cell_ids[ci] = ((unsigned long long)i * N + j) * N + k;
+                    out.cell_cases[ci] = (uint8_t)cs;
+                }
+            }
+        } else if (sm && lane == 0) {
+            atomicAdd(&s.ctr->cells, (unsigned long long)__popc(sm));
+        }
+        for (int t = 0; t < nt; ++t) {
+            const unsigned long long ti = tbase + t;
+            if (ti >= (unsigned long long)out.capacity_tris) break;
+            float pos[9];
+            unsigned long long key[3];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const int e = c_tab_e[cs][3 * t + v];
+                const int ax = e >> 2, u = e & 1, w = (e >> 1) & 1;
+                const int ox = ax == 0 ? 0 : u, oy = ax == 1 ? 0 : (ax == 0 ? u : w), oz = ax == 2 ? 0 : w;
+                const int blo = ox + 2 * oy + 4 * oz, bhi = blo + (1 << ax);
+                const float fa = fv[blo], fb = fv[bhi];
+                const float tt = fa / (fa - fb);
+                const int la = i + ox, lb = j + oy, lc = k + oz;
+                float px = fmaf((float)la, g.h, g.lo[0]);
+                float py = fmaf((float)lb, g.h, g.lo[1]);
+                float pz = fmaf((float)lc, g.h, g.lo[2]);
+                if (ax == 0) px = fmaf(tt, g.h, px);
+                else if (ax == 1) py = fmaf(tt, g.h, py);
+                else pz = fmaf(tt, g.h, pz);
+                pos[3 * v] = px;
+                pos[3 * v + 1] = py;
+                pos[3 * v + 2] = pz;
+                key[v] = (unsigned long long)ax * N13 + (unsigned long long)la +
+                         (unsigned long long)N1 * ((unsigned long long)lb + (unsigned long long)N1 * lc);
+            }
+            float *dst = out.tri_xyz + ti * 9;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dst[q] = pos[q];
+            if (out.tri_keys) {
+                unsigned long long *kd = reinterpret_cast<unsigned long long *>(out.tri_keys) + ti * 3;
+                kd[0] = key[0];
+                kd[1] = key[1];
+                kd[2] = key[2];
+            }
+        }
+    }
+}
+
+void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st) {
+    k_mc<<<nsm * 8, 256, 0, st>>>(g, s, out);
+}
+
+// ---------------------------------------------------------------------------
+// Results: counts, statistics and the status word.
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
+    const Counters c = *s.ctr;
+    long long status = GH_OK;
+    if (c.flags & FLAG_NONFINITE) status = GH_ERR_NONFINITE;
+    if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) status = GH_ERR_CAPACITY;
+    if (c.tris > (unsigned long long)out.capacity_tris) status = GH_ERR_CAPACITY;
+    if (out.cell_ids && c.cells > (unsigned long long)out.capacity_cells) status = GH_ERR_CAPACITY;
+    if (out.n_tris) *out.n_tris = (long long)c.tris;
+    if (out.n_cells) *out.n_cells = (long long)c.cells;
+    if (out.stats) {
+        gh_stats *st = out.stats;
+        st->status = status;
+        st->columns = columns;
+        st->hop_evals = (long long)c.hop_evals;
+        st->marked_cells = (long long)c.marks;
+        st->unique_vertices = (long long)c.verts;
+        st->refined_vertices = (long long)c.refine;
+        st->surface_cells = (long long)c.cells;
+        st->triangles = (long long)c.tris;
+    }
+}
+
+void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st) {
+    k_finalize<<<1, 1, 0, st>>>(s, out, columns);
+}
+
+}  // namespace gh

@@ -1,0 +1,133 @@
+"""GPU parity of the analytic-SDB path (hopper + Marching Cubes kernels)
+against the FP64 oracle, through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2111_05778_gb300 import gh, synth  # noqa: E402
+
+
+def _golden(N):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sphere_r05_counts.txt")
+    for l in open(path):
+        if l.strip() and not l.startswith("#"):
+            r = list(map(int, l.split()))
+            if r[0] == N:
+                return r
+    raise KeyError(N)
+
+
+@pytest.mark.parametrize("N", [16, 64, 256])
+def test_sphere_matches_oracle(N):
+    prims = synth.sphere_prims(0.5)
+    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    o = oracle.csg(prims)
+    _, ref = oracle.polygonize(o, N)
+    st = parity.compare(m, o, N, ref=ref)
+    g = _golden(N)
+    assert m.stats["surface_cells"] == g[4]
+    assert m.n_tris == g[6]
+    assert m.stats["marked_cells"] == g[2]
+    assert m.stats["hop_evals"] == g[1]
+    assert st["tie_cells"] <= 24
+
+
+@pytest.mark.parametrize("N,lo,hi", [(37, -1.0, 1.0), (100, -0.7, 0.9), (2, -1.0, 1.0), (129, -0.61, 0.61)])
+def test_ragged_and_offset_grids(N, lo, hi):
+    prims = np.concatenate([synth.sphere_prims(0.45, (0.05, -0.1, 0.02)),
+                            synth.prim_row(synth.TORUS, synth.UNION, [0.1, 0.2, -0.1], [0.3, 0.08])[None]])
+    m = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True, cells=True)
+    o = oracle.csg(prims)
+    ref = oracle.enum(o, N, lo, hi)
+    parity.compare(m, o, N, lo, hi, ref=ref)
+
+
+@pytest.mark.parametrize("tau_mode", [0, 1])
+def test_csg_scene_full(tau_mode):
+    prims = synth.csg_prims(0)
+    N = 160
+    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True, tau_mode=tau_mode)
+    o = oracle.csg(prims)
+    ref = oracle.enum(o, N)
+    st = parity.compare(m, o, N, ref=ref)
+    assert st["cells"] > 10000
+
+
+def test_csg_c1_sampled_columns_n512():
+    """The C1 workload (CSG seed 0, N = 512) at full size: every sign-change
+    cell of 400 random columns and of two full z-slabs, checked cell by cell."""
+    prims = synth.csg_prims(0)
+    N = 512
+    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    o = oracle.csg(prims)
+    rng = np.random.default_rng(11)
+    cols = np.unique(rng.choice(N * N, 400, replace=False))
+    _, ref = oracle.polygonize(o, N, cols=cols)
+    parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols))
+    for k0 in (173, 301):
+        ref = oracle.enum(o, N, kmin=k0, kmax=k0 + 1)
+        parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: (c % N) == k0)
+
+
+def test_no_surface_inside_domain():
+    for prims in (synth.sphere_prims(0.2, (5.0, 5.0, 5.0)), synth.sphere_prims(10.0)):
+        m = gh.polygonize(gh.CsgSdb(prims), 64, keys=True, cells=True)
+        assert m.n_tris == 0 and m.cell_ids.numel() == 0
+        assert m.stats["status"] == 0
+
+
+def test_capacity_protocol():
+    sdb = gh.CsgSdb(synth.sphere_prims(0.5))
+    N = 64
+    bufs = gh.Buffers(100, keys=True)
+    rc = gh.polygonize_into(sdb, N, bufs)
+    assert rc == gh.GH_ERR_CAPACITY
+    need = int(bufs.counts[0].item())
+    assert need == _golden(N)[6]
+    bufs = gh.Buffers(need, keys=True)
+    assert gh.polygonize_into(sdb, N, bufs) == gh.GH_OK
+    assert int(bufs.counts[0].item()) == need
+
+
+def test_invalid_arguments():
+    sdb = gh.CsgSdb(synth.sphere_prims(0.5))
+    bufs = gh.Buffers(1000)
+    for N in (1, 4096):
+        with pytest.raises(gh.GhError) as e:
+            gh.polygonize_into(sdb, N, bufs)
+        assert e.value.code == gh.GH_ERR_ARG
+    with pytest.raises(gh.GhError):
+        gh.polygonize_into(sdb, 32, bufs, lo=[-1, -1, -1], hi=[1, 1, 2])
+    with pytest.raises(gh.GhError) as e:
+        gh.polygonize_into(sdb, 32, bufs, precision="bf16")
+    assert e.value.code == gh.GH_ERR_ARG
+    bad = synth.sphere_prims(0.5).copy()
+    bad[0, 0] = 7
+    with pytest.raises(gh.GhError):
+        gh.CsgSdb(bad)
+
+
+def test_repeat_calls_are_identical():
+    sdb = gh.CsgSdb(synth.csg_prims(2))
+    a = gh.polygonize(sdb, 96, keys=True)
+    b = gh.polygonize(sdb, 96, keys=True)
+    import meshutil
+    ka = meshutil.canonical_tris(a.tri_keys.cpu().numpy())
+    kb = meshutil.canonical_tris(b.tri_keys.cpu().numpy())
+    assert (ka == kb).all()
+
+
+def test_eval_points_matches_oracle():
+    prims = synth.csg_prims(0)
+    sdb = gh.CsgSdb(prims)
+    P = synth.uniform_points(3, 100000)
+    f = gh.eval_points(sdb, torch.from_numpy(P).cuda()).cpu().numpy()
+    ref = oracle.csg(prims).eval(P.astype(np.float64))
+    assert np.abs(f - ref).max() < parity.DELTA32

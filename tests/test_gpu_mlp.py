@@ -1,0 +1,52 @@
+"""GPU parity of the neural-SDB path (FP32 on the FFMA pipe) against the
+FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2111_05778_gb300 import gh, synth  # noqa: E402
+
+
+def _pair(seed, width):
+    p = synth.mlp_params(seed, width)
+    return gh.MlpSdb(p, width), oracle.mlp(width, synth.MLP_NMID, p.astype(np.float64))
+
+
+@pytest.mark.parametrize("width", [64, 128, 256])
+def test_eval_fp32_pointwise(width):
+    sdb, o = _pair(1, width)
+    P = synth.uniform_points(5, 20000)
+    f = gh.eval_points(sdb, torch.from_numpy(P).cuda()).cpu().numpy()
+    assert np.abs(f - o.eval(P.astype(np.float64))).max() < 1e-6
+
+
+@pytest.mark.parametrize("width,N", [(64, 40), (128, 48), (256, 56)])
+def test_mlp_fp32_full(width, N):
+    sdb, o = _pair(1 + width, width)
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
+    ref = oracle.enum(o, N)
+    st = parity.compare(m, o, N, ref=ref)
+    assert st["cells"] > 1000
+
+
+def test_mlp_c2_fp32_sampled_n1024():
+    """The C2 network (seed 1, width 256) at N = 1024 in FP32: the sign-change
+    cells of 48 random columns, checked cell by cell against the oracle."""
+    sdb, o = _pair(1, 256)
+    N = 1024
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
+    rng = np.random.default_rng(7)
+    # columns through the middle of the domain so that they cross the surface
+    i = rng.integers(300, 724, 48)
+    j = rng.integers(300, 724, 48)
+    cols = np.unique(i * N + j)
+    _, ref = oracle.polygonize(o, N, cols=cols)
+    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols))
+    assert st["cells"] > 40
+    s = m.stats
+    assert s["surface_cells"] > 1_000_000
