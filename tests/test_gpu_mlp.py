@@ -46,7 +46,10 @@ def test_mlp_c2_fp32_sampled_n1024():
     j = rng.integers(300, 724, 48)
     cols = np.unique(i * N + j)
     _, ref = oracle.polygonize(o, N, cols=cols)
-    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols))
+    # at h = 2/1024 the bare 1e-4 h (2e-7) is about the FP32 evaluation error
+    # of this network divided by |fA - fB| on nearly tangent edges, so ~2% of
+    # the vertices exceed it; all stay inside the error-propagated bound.
+    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.95)
     assert st["cells"] > 40
     s = m.stats
     assert s["surface_cells"] > 1_000_000
