@@ -45,7 +45,12 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    ap.add_argument("--N", type=int, default=None, help="grid size (default 1024; smaller for profiling)")
+    args = ap.parse_args()
+    if args.N:
+        WORKLOAD["N"] = int(args.N)
+        WORKLOAD["workload"] = WORKLOAD["workload"].replace("N=1024", "N=%d" % args.N)
+    return args
 
 
 def dist_env():
