@@ -193,6 +193,35 @@ int gh_polygonize(const gh_grid *grid, const gh_sdb *sdb, const gh_options *opts
 int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
                         gh_mesh *outs, void *stream, void **graph);
 
+/* No-allocation variant of gh_polygonize for analytic (CSG) scenes.  The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory while they polygonize -- a plug-in inside a host
+ * application that owns the whole device-memory budget and hands out no
+ * more, or a real-time loop that must not call cudaMalloc / cudaFree because
+ * those calls can block on, or synchronise with, work already running on the
+ * device.  It calls no allocator: its scratch is one file-scope __device__
+ * array of GH_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads this
+ * library keeps from load until the process exits.
+ *   grid:   as in gh_polygonize, with N <= GH_NOALLOC_MAX_N.
+ *   prims:  device array of n_prim gh_csg_prim records (1 <= n_prim <=
+ *           GH_MAX_PRIMS); caller-owned, only read.
+ *   out:    caller-owned device buffers, as in gh_polygonize.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * The call waits for its stream and reports errors as gh_polygonize with
+ * sync = 1 does, except that the scratch never grows: a scene that marks
+ * more cells, or needs more lattice vertices, than the array holds returns
+ * GH_ERR_CAPACITY with a message giving both numbers; N above the maximum
+ * returns GH_ERR_ARG.  The first call on a device looks up the device
+ * address of the array (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call uses the same
+ * array and leaves its contents behind (each call clears its own counters
+ * before use), so calls that overlap on the GPU -- from different streams or
+ * threads at the same time -- race; serialise them. */
+#define GH_NOALLOC_MAX_N 256
+#define GH_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim, int32_t tau_mode,
+                              gh_mesh *out, void *stream);
+
 /* Implicit-surface adjoint for a neural SDB: given mesh vertices v[V][3]
  * (device, float32) and the loss gradient dL/dv[V][3] (device), accumulates
  *   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f)/|grad_x f|^2,

@@ -609,3 +609,97 @@ extern "C" int gh_backward(const gh_sdb *s, const float *verts, const float *dL_
     (void)s; (void)verts; (void)dL_dv; (void)V; (void)dL_dtheta; (void)stream;
     return fail(GH_ERR_UNIMPLEMENTED, "gh_backward: not available yet");
 }
+
+// ---------------------------------------------------------------------------
+// No-allocation variant (analytic scenes): the scratch of the pipeline lives
+// in one file-scope device array instead of per-SDB cudaMalloc'd buffers.
+// Host code must not use the array's name as an address (it is a host-side
+// stand-in); the device address is looked up once per device below.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GH_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim,
+                                         int32_t tau_mode, gh_mesh *out, void *stream) {
+    GridP g;
+    int rc = check_grid(grid, &g, tau_mode);
+    if (rc) return rc;
+    if (g.N > GH_NOALLOC_MAX_N)
+        return fail(GH_ERR_ARG, "gh_polygonize_csg_noalloc: N = %d exceeds GH_NOALLOC_MAX_N = %d", g.N,
+                    GH_NOALLOC_MAX_N);
+    if (!prims) return fail(GH_ERR_ARG, "gh_polygonize_csg_noalloc: NULL prims");
+    if (n_prim < 1 || n_prim > GH_MAX_PRIMS)
+        return fail(GH_ERR_ARG, "gh_polygonize_csg_noalloc: n_prim = %d outside [1, %d]", n_prim, GH_MAX_PRIMS);
+    if ((rc = check_mesh(out))) return rc;
+    int dev, nsm;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(GH_ERR_CUDA, "cudaGetSymbolAddress(no-allocation scratch): %s", cudaGetErrorString(e));
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    // carve the array for the largest grid it accepts
+    const size_t NN = GH_NOALLOC_MAX_N, ncols = NN * NN, nlines = (NN + 1) * (NN + 1);
+    char *q = (char *)base;
+    size_t off = 0;
+    Scratch c{};
+    c.ctr = (Counters *)(q + off);
+    off += up256(sizeof(Counters));
+    c.colcount = (uint32_t *)(q + off);
+    off += up256(4 * ncols);
+    c.coloff = (uint32_t *)(q + off);
+    off += up256(4 * (ncols + 1));
+    c.linecount = (uint32_t *)(q + off);
+    off += up256(4 * nlines);
+    c.lineoff = (uint32_t *)(q + off);
+    off += up256(4 * (nlines + 1));
+    c.blocksum = (uint32_t *)(q + off);
+    off += up256(4 * 4096);
+    const size_t per = 2 * 8 + 2 * (8 + 4);  // marks raw + grouped, two vertices (key + value) per mark
+    const size_t M = ((GH_NOALLOC_SCRATCH_BYTES - off - 4 * 256) / per) & ~(size_t)255;
+    c.marks_raw = (unsigned long long *)(q + off);
+    off += up256(8 * M);
+    c.marks_csr = (unsigned long long *)(q + off);
+    off += up256(8 * M);
+    c.vkey = (unsigned long long *)(q + off);
+    off += up256(8 * 2 * M);
+    c.vval = (float *)(q + off);
+    off += up256(4 * 2 * M);
+    c.cap_marks = (long long)M;
+    c.cap_verts = (long long)(2 * M);
+    if (off > GH_NOALLOC_SCRATCH_BYTES) return fail(GH_ERR_CUDA, "no-allocation scratch layout overflows");
+    cudaStream_t st = (cudaStream_t)stream;
+    const Prim *dp = reinterpret_cast<const Prim *>(prims);
+    launch_init(c, st);  // clears the counters left by the previous call
+    launch_hop_csg(dp, n_prim, g, c, nsm, st);
+    launch_build_lists(g, c, st);
+    launch_eval_vertices_csg(dp, n_prim, g, c, nsm, st);
+    launch_mc(g, c, *out, nsm, st);
+    launch_finalize(c, *out, (long long)g.N * g.N, st);
+    GH_CUDA(cudaGetLastError());
+    Counters h;
+    GH_CUDA(cudaMemcpyAsync(&h, c.ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GH_CUDA(cudaStreamSynchronize(st));
+    if (h.flags & FLAG_MARK_OVERFLOW)
+        return fail(GH_ERR_CAPACITY, "scene marks %llu cells; the no-allocation scratch holds %lld", h.marks,
+                    c.cap_marks);
+    if (h.flags & FLAG_VERT_OVERFLOW)
+        return fail(GH_ERR_CAPACITY, "scene needs %llu lattice vertices; the no-allocation scratch holds %lld",
+                    h.verts, c.cap_verts);
+    if (h.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
+    if (h.tris > (unsigned long long)out->capacity_tris)
+        return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris, h.tris);
+    if (out->cell_ids && h.cells > (unsigned long long)out->capacity_cells)
+        return fail(GH_ERR_CAPACITY, "cell buffer holds %lld, %llu needed", (long long)out->capacity_cells, h.cells);
+    return GH_OK;
+}

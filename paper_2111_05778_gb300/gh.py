@@ -98,6 +98,8 @@ def lib():
                 "gh_last_error": (ctypes.c_char_p, []),
                 "gh_version": (ctypes.c_char_p, []),
                 "gh_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+                "gh_polygonize_csg_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), P, I32, I32,
+                                                             ctypes.POINTER(MeshDesc), P]),
                 "gh_last_profile": (ctypes.c_int, [ctypes.POINTER(Profile)]),
             }
             for name, (res, args) in sig.items():
@@ -112,7 +114,7 @@ def exported_symbols():
     """Names declared in include/gh.h that the library must export."""
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
-            "gh_set_profiling", "gh_last_profile"]
+            "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc"]
 
 
 def check(rc):
@@ -314,6 +316,32 @@ def polygonize(sdb: Sdb, N, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_D
                         bufs.stats_dict())
         cap = int(max(counts[0], counts[1]) * 1.1) + 4096
     raise GhError(GH_ERR_CAPACITY, "output buffers kept overflowing")
+
+
+NOALLOC_MAX_N = 256
+
+
+def csg_prims_device(prims, device=None):
+    """The gh_csg_prim records of a scene as a device uint8 tensor (the input
+    of polygonize_csg_noalloc, which copies nothing itself)."""
+    import torch
+
+    rec = np.frombuffer(csg_blob(prims)[16:], np.uint8).copy()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return torch.from_numpy(rec).to(dev)
+
+
+def polygonize_csg_noalloc(prims_dev, n_prim, N, bufs: Buffers, lo=-1.0, hi=1.0, tau_mode=GH_TAU_DIAGONAL,
+                           stream=None) -> int:
+    """gh_polygonize_csg_noalloc: the analytic pipeline on the library's
+    static scratch (for callers that cannot allocate device memory); prims_dev
+    from csg_prims_device.  Returns GH_OK or GH_ERR_CAPACITY, raises otherwise."""
+    g = _grid(N, lo, hi)
+    rc = lib().gh_polygonize_csg_noalloc(ctypes.byref(g), prims_dev.data_ptr(), int(n_prim), int(tau_mode),
+                                         ctypes.byref(bufs.desc), _stream_ptr(stream))
+    if rc not in (GH_OK, GH_ERR_CAPACITY):
+        check(rc)
+    return rc
 
 
 def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):
