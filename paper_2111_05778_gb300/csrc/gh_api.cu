@@ -300,10 +300,35 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
                     }
         for (int o = 0; o < W; ++o) bm[(size_t)l * W + o] = bl[o];
     }
+    // BF16 hidden weights for the tensor cores: per layer, K-blocks of 64 inputs;
+    // a K-block holds W rows (outputs) of 128 bytes in the 128-byte swizzled
+    // K-major layout the MMA reads from shared memory: row n, 16-byte chunk c
+    // of inputs [8c, 8c+8) lands at (n/8)*1024 + (n%8)*128 + ((c ^ n%8) * 16).
+    const int KB = W / 64;
+    std::vector<uint16_t> wbf((size_t)h.n_mid * W * W);
+    for (int l = 0; l < h.n_mid; ++l) {
+        const float *Wl = mid + (size_t)l * ((size_t)W * W + W);
+        for (int kb = 0; kb < KB; ++kb) {
+            uint16_t *blk = wbf.data() + ((size_t)l * KB + kb) * (size_t)W * 64;
+            for (int n = 0; n < W; ++n)
+                for (int kk = 0; kk < 64; ++kk) {
+                    const size_t byte = (size_t)(n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7))) << 4) +
+                                        (kk & 7) * 2;
+                    uint32_t u;
+                    const float v = Wl[(size_t)n * W + kb * 64 + kk];
+                    memcpy(&u, &v, 4);
+                    u = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;  // round to nearest even
+                    blk[byte / 2] = (uint16_t)u;
+                }
+        }
+    }
     float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout;
+    uint16_t *d_wbf;
     if (dev_alloc(s, &d_w0, 3 * W) || dev_alloc(s, &d_b0, W) || dev_alloc(s, &d_wt, wt.size()) ||
-        dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np))
+        dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np) ||
+        dev_alloc(s, &d_wbf, wbf.size()))
         return GH_ERR_CUDA;
+    GH_CUDA(cudaMemcpy(d_wbf, wbf.data(), sizeof(uint16_t) * wbf.size(), cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_w0, W0, sizeof(float) * 3 * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_b0, B0, sizeof(float) * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
@@ -323,7 +348,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.bm = d_bm;
     m.wout = d_wout;
     m.bout = wout[W];
-    m.wbf = nullptr;
+    m.wbf = d_wbf;
     s->nparam = np;
     return GH_OK;
 }
@@ -473,7 +498,7 @@ static inline void mark_phase(int i, cudaStream_t st) {
 }
 
 // Kernel launches per phase (fixed by the launch sequence below).
-static constexpr int LAUNCHES_HOP = 2, LAUNCHES_LISTS = 8, LAUNCHES_VERTS = 1, LAUNCHES_REFINE = 2,
+static constexpr int LAUNCHES_HOP = 2, LAUNCHES_LISTS = 8, LAUNCHES_VERTS = 1, LAUNCHES_REFINE = 4,
                      LAUNCHES_MC = 2;
 
 static int enqueue_once(gh_sdb *s, const GridP &g, int precision, const gh_mesh &out, int nsm, cudaStream_t st) {
@@ -559,6 +584,7 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
             if (want_v < 2 * want_m) want_v = 2 * want_m;
             continue;
         }
+        if (c.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
         if (c.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
         if (c.tris > (unsigned long long)out->capacity_tris)
             return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris,
@@ -592,10 +618,80 @@ extern "C" int gh_eval(const gh_sdb *s, const float *p, int64_t n, float *out, i
     return GH_OK;
 }
 
+// max |f_bf16 - f_fp32| over n points p[n][3] (device); d_max is a device uint.
+static int bf16_gap(gh_sdb *s, const float *p, long long n, float *f32, float *f16, unsigned int *d_max, int nsm,
+                    cudaStream_t st) {
+    if (n <= 0) return GH_OK;
+    launch_eval_points_mlp_fp32(s->mlp, p, n, f32, nsm, st);
+    launch_eval_points_mlp_bf16(s->mlp, p, n, f16, nsm, st);
+    launch_max_abs_diff(f32, f16, n, d_max, st);
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
+}
+
 extern "C" int gh_sdb_calibrate(gh_sdb *s, const gh_grid *grid, int64_t n_points, uint64_t seed, float *eps_out,
                                 void *stream) {
-    (void)s; (void)grid; (void)n_points; (void)seed; (void)eps_out; (void)stream;
-    return fail(GH_ERR_UNIMPLEMENTED, "gh_sdb_calibrate: not available yet");
+    if (!s || s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "gh_sdb_calibrate needs a neural SDB");
+    if (n_points < 0 || n_points > (1ll << 26)) return fail(GH_ERR_ARG, "n_points outside [0, 2^26]");
+    GridP g;
+    int rc = check_grid(grid, &g, GH_TAU_DIAGONAL);
+    if (rc) return rc;
+    int dev, nsm;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(s->mu);
+    // 1. seeded uniform points of the polygonization volume
+    // 2. the lattice vertices a plain FP32 run needs at a quarter of the
+    //    resolution -- points next to the surface, where eps matters most
+    GridP gc = g;
+    gc.N = g.N / 4 < 32 ? 32 : g.N / 4;
+    gc.h = (g.h * g.N) / gc.N;
+    gc.inv_h = 1.f / gc.h;
+    gc.tau = (float)(sqrt(3.0) * gc.h);
+    gc.eps = 0.f;
+    const long long N2 = (long long)gc.N * gc.N;
+    if ((rc = ensure_scratch(s, gc.N, 8 * N2 > (1 << 16) ? 8 * N2 : (1 << 16), 16 * N2 > (1 << 17) ? 16 * N2 : (1 << 17))))
+        return rc;
+    Scratch &c = s->scr;
+    launch_init(c, st);
+    launch_hop_mlp_fp32(s->mlp, gc, c, nsm, st);
+    launch_build_lists(gc, c, st);
+    Counters hc;
+    GH_CUDA(cudaMemcpyAsync(&hc, c.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    GH_CUDA(cudaStreamSynchronize(st));
+    const long long nv = (hc.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) ? 0 : (long long)hc.verts;
+    const long long nmax = n_points > nv ? n_points : nv;
+    float *p = nullptr, *f32 = nullptr, *f16 = nullptr;
+    unsigned int *d_max = nullptr;
+    GH_CUDA(cudaMalloc((void **)&p, sizeof(float) * 3 * (nmax + 1)));
+    GH_CUDA(cudaMalloc((void **)&f32, sizeof(float) * (nmax + 1)));
+    GH_CUDA(cudaMalloc((void **)&f16, sizeof(float) * (nmax + 1)));
+    GH_CUDA(cudaMalloc((void **)&d_max, sizeof(unsigned int)));
+    GH_CUDA(cudaMemsetAsync(d_max, 0, sizeof(unsigned int), st));
+    const float ext = g.h * (float)g.N;
+    launch_rand_points(p, n_points, g.lo, ext, seed, st);
+    rc = bf16_gap(s, p, n_points, f32, f16, d_max, nsm, st);
+    if (!rc && nv > 0) {
+        launch_vertex_points(gc, c, p, st);
+        rc = bf16_gap(s, p, nv, f32, f16, d_max, nsm, st);
+    }
+    unsigned int hmax = 0;
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(GH_ERR_CUDA, "calibration: %s", cudaGetErrorString(e));
+    }
+    cudaFree(p);
+    cudaFree(f32);
+    cudaFree(f16);
+    cudaFree(d_max);
+    if (rc) return rc;
+    float gap;
+    memcpy(&gap, &hmax, 4);
+    if (!isfinite(gap)) return fail(GH_ERR_NONFINITE, "calibration met a non-finite value");
+    s->eps = 2.f * gap;
+    if (eps_out) *eps_out = s->eps;
+    return GH_OK;
 }
 
 extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,

@@ -29,6 +29,7 @@ enum : unsigned long long {
     FLAG_TRI_OVERFLOW = 4ull,    // caller's triangle buffer too small
     FLAG_CELL_OVERFLOW = 8ull,   // caller's cell buffer too small
     FLAG_NONFINITE = 16ull,      // f was NaN or inf somewhere
+    FLAG_TIMEOUT = 32ull,        // a bounded device wait gave up
 };
 
 // Grid parameters as the kernels see them (FP32).
@@ -114,6 +115,11 @@ void launch_hop_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, c
 void launch_eval_vertices_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
-void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);
+void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);  // k_pipeline.cu
+
+// calibration helpers (k_pipeline.cu)
+void launch_rand_points(float *p, long long n, const float *lo, float ext, unsigned long long seed, cudaStream_t st);
+void launch_vertex_points(const GridP &g, Scratch &s, float *p, cudaStream_t st);
+void launch_max_abs_diff(const float *a, const float *b, long long n, unsigned int *out, cudaStream_t st);
 
 }  // namespace gh

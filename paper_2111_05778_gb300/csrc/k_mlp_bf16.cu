@@ -1,11 +1,538 @@
-// Neural SDB in BF16 on the tcgen05 tensor cores (placeholder until the
-// tensor-core kernels land; bf16_supported() reports false).
+// Neural SDB in BF16 on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// f(p) = (|p| - r0 + alpha g(p)) / beta / lambda, g a ReLU MLP (the neural
+// SDB of Sec. 5.2).  The W x W hidden layers run as tcgen05.mma GEMMs with
+// BF16 operands and FP32 accumulation in tensor memory; layer 0 (3 -> W) and
+// the output layer (W -> 1) run on CUDA cores in FP32.
+//
+// One persistent CTA per SM, 384 threads:
+//   warp 0       TMA producer: 1-D bulk copies (cp.async.bulk) of BF16 weight
+//                K-blocks, stored pre-swizzled in global memory, into a
+//                2-stage shared-memory ring (mbarrier complete_tx).
+//   warp 1       allocates TMEM; one lane issues tcgen05.mma for two 128-row
+//                tiles per weight K-block (M = 128, N = W, K = 16 per op) and
+//                tcgen05.commit's to the ring's "empty" barriers and to the
+//                accumulator barrier.
+//   warps 4..11  epilogue, one row (one ray or one point) per thread: layer 0,
+//                TMEM -> registers (tcgen05.ld) -> bias, ReLU, BF16 -> the next
+//                layer's A operand in 128B-swizzled K-major shared memory,
+//                the FP32 output dot product, and the grid-hopping step of
+//                Algorithm 1 (with the eps shrink) or the store of f.
+// Every wait is bounded (2 s of %globaltimer); a timeout sets an error flag,
+// makes all roles leave their loops, drains the copies in flight, and frees
+// TMEM before the kernel returns.
+#include <stdint.h>
+
 #include "gh_internal.cuh"
 
 namespace gh {
-bool bf16_supported(int) { return false; }
-void launch_hop_mlp_bf16(const MlpDev &, const GridP &, Scratch &, int, cudaStream_t) {}
-void launch_eval_vertices_mlp_bf16(const MlpDev &, const GridP &, Scratch &, int, cudaStream_t) {}
-void launch_eval_points_mlp_bf16(const MlpDev &, const float *, long long, float *, int, cudaStream_t) {}
-void launch_refine_select(const GridP &, Scratch &, cudaStream_t) {}
+
+namespace {
+
+constexpr int NTHREADS = 384;
+constexpr int EPI_T0 = 128;  // first epilogue thread (warp 4)
+constexpr int NEPI = 256;    // epilogue threads = rows per step
+constexpr int TM = 128;      // rows per tile
+constexpr int NSTAGE = 2;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+constexpr int CTL_STOP = 1, CTL_ABORT = 2;
+
+enum { MODE_HOP = 0, MODE_VERTS = 1, MODE_POINTS = 2 };
+
+template <int W>
+struct SmemB {
+    uint8_t a[2][W / 64][TM * 128];  // A operands: 2 tiles, K-blocks of 128 rows x 128 B (1024-aligned)
+    uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
+    float4 w0b[W];                   // layer 0: W0 row and bias
+    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full, a_full, drain;
+    uint32_t tmem_base;
+    int ctl;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity.  Returns false without waiting
+// further once (ctl & give_up) is set; on a 2 s timeout sets the abort bit
+// and the device error flag and returns false.
+__device__ __noinline__ bool wait_bar(unsigned long long *b, uint32_t parity, volatile int *ctl, int give_up,
+                                      Counters *ctr) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(b, parity)) return true;
+        if (*ctl & give_up) return false;
+        if ((it & 255) == 0 && gtimer() - t0 > WAIT_NS) {
+            atomicOr((int *)ctl, CTL_ABORT);
+            atomicOr(&ctr->flags, FLAG_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ unsigned long long sdesc(uint32_t saddr) {
+    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+// kind::f16 instruction descriptor: F32 accumulate, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// OR-reduction over the 256 epilogue threads (named barrier 1).
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)v)
+        : "memory");
+    return out != 0;
+}
+
+__device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, float z, float g) {
+    const float r = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
+    return (fmaf(m.alpha, g, r - m.r0) / m.beta) * m.inv_lam;
+}
+
+// ---------------------------------------------------------------------------
+template <int W, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_mlp_bf16(MlpDev m, GridP g, Scratch s, const float *__restrict__ pts, long long npts, float *__restrict__ outv) {
+    extern __shared__ uint8_t smem_raw[];
+    constexpr int KB = W / 64;
+    constexpr uint32_t STAGE_BYTES = W * 128;
+    constexpr uint32_t TMEM_COLS = 2 * W;
+    constexpr uint32_t IDESC = idesc_bf16(TM, W);
+    SmemB<W> &sm = *reinterpret_cast<SmemB<W> *>(smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (MODE == MODE_VERTS && (s.ctr->flags & STOP_FLAGS)) return;  // uniform: nothing to evaluate
+    volatile int *ctl = &sm.ctl;
+
+    // ---- set-up ----------------------------------------------------------
+    if (tid < W)
+        sm.w0b[tid] = make_float4(m.w0[3 * tid], m.w0[3 * tid + 1], m.w0[3 * tid + 2], m.b0[tid]);
+    if (tid == 0) {
+        for (int i = 0; i < NSTAGE; ++i) {
+            mbar_init(&sm.full[i], 1);
+            mbar_init(&sm.empty[i], 1);
+        }
+        mbar_init(&sm.acc_full, 1);
+        mbar_init(&sm.a_full, NEPI);
+        mbar_init(&sm.drain, 1);
+        sm.ctl = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sm.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+
+    if (warp == 0) {
+        // ---- TMA producer ----------------------------------------------------
+        if (lane == 0) {
+            const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(m.wbf);
+            const int nblk = m.n_mid * KB;
+            long long issued = 0;
+            for (int blk = 0;; blk = (blk + 1 == nblk) ? 0 : blk + 1) {
+                const int st = (int)(issued % NSTAGE);
+                const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
+                if (!wait_bar(&sm.empty[st], par, ctl, CTL_STOP | CTL_ABORT, s.ctr)) break;
+                mbar_expect_tx(&sm.full[st], STAGE_BYTES);
+                bulk_g2s(sm.w[st], wsrc + (size_t)blk * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
+                ++issued;
+            }
+            // the copies still in flight land before the CTA may exit
+            for (long long i = issued - NSTAGE; i < issued; ++i) {
+                if (i < 0) continue;
+                wait_bar(&sm.full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), ctl, 0, s.ctr);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer --------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t a0 = su32(&sm.a[0][0][0]), a1 = su32(&sm.a[1][0][0]);
+            long long consumed = 0;
+            uint32_t pa = 0;
+            bool go = true;
+            while (go) {
+                for (int l = 0; l < m.n_mid && go; ++l) {
+                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, s.ctr) || (*ctl & CTL_STOP)) {
+                        go = false;
+                        break;
+                    }
+                    pa ^= 1u;
+                    tc_fence_after();
+                    for (int kb = 0; kb < KB; ++kb) {
+                        const int st = (int)(consumed % NSTAGE);
+                        if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, s.ctr)) {
+                            go = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t wb = su32(sm.w[st]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const unsigned long long bd = sdesc(wb + k * 32);
+                            umma(tmem, sdesc(a0 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
+                            umma(tmem + W, sdesc(a1 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
+                        }
+                        umma_commit(&sm.empty[st]);
+                        ++consumed;
+                    }
+                    if (go) umma_commit(&sm.acc_full);
+                }
+            }
+            // every MMA issued above has completed before TMEM is released
+            umma_commit(&sm.drain);
+            wait_bar(&sm.drain, 0, ctl, 0, s.ctr);
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---- epilogue: one row per thread ------------------------------------
+        const int et = tid - EPI_T0, t = et >> 7, row = et & (TM - 1), q = (warp - 4) & 3;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * W);
+        const uint32_t arow = su32(&sm.a[t][0][0]) + (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
+        const int sw = row & 7;
+        const unsigned lt = (1u << lane) - 1u;
+        const int N = g.N;
+        const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+        uint32_t col = NONE, rank = 0;
+        int k = 0;
+        bool done = false;
+        float x = 0.f, y = 0.f;
+        unsigned long long evals = 0, idx = 0;
+        uint32_t pacc = 0;
+        for (;;) {
+            // 1. the work of this row
+            bool live = false;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            if (MODE == MODE_HOP) {
+                const bool need = col == NONE && !done;
+                const unsigned needm = __ballot_sync(FULL, need);
+                if (needm) {
+                    const int leader = __ffs(needm) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
+                    base = __shfl_sync(FULL, base, leader);
+                    if (need) {
+                        const unsigned long long c = base + __popc(needm & lt);
+                        if (c < ncols) {
+                            col = (uint32_t)c;
+                            k = 0;
+                            rank = 0;
+                            const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                            x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                            y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                        } else {
+                            done = true;
+                        }
+                    }
+                }
+                live = col != NONE;
+                if (live) {
+                    px = x;
+                    py = y;
+                    pz = fmaf((float)k + 0.5f, g.h, g.lo[2]);
+                }
+            } else {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&s.ctr->next_tile, 32ull);
+                base = __shfl_sync(FULL, base, 0);
+                idx = base + lane;
+                const unsigned long long total = MODE == MODE_VERTS ? s.ctr->verts : (unsigned long long)npts;
+                live = idx < total;
+                if (live) {
+                    if (MODE == MODE_POINTS) {
+                        px = pts[3 * idx];
+                        py = pts[3 * idx + 1];
+                        pz = pts[3 * idx + 2];
+                    } else {
+                        const unsigned long long key = s.vkey[idx];
+                        const int N1 = g.N + 1;
+                        const uint32_t line = (uint32_t)(key & 0xFFFFFFFFull), c = (uint32_t)(key >> 32);
+                        const uint32_t a = line / (uint32_t)N1, b = line - a * (uint32_t)N1;
+                        px = fmaf((float)a, g.h, g.lo[0]);
+                        py = fmaf((float)b, g.h, g.lo[1]);
+                        pz = fmaf((float)c, g.h, g.lo[2]);
+                    }
+                }
+            }
+            __syncwarp();
+            const bool any = epi_any(live);
+            if (!any || (*ctl & CTL_ABORT)) {
+                if (et == 0) {
+                    *ctl |= CTL_STOP;
+                    __threadfence_block();
+                }
+                epi_any(false);  // the stop bit is written before anyone arrives
+                mbar_arrive(&sm.a_full);
+                break;
+            }
+            // 2. layer 0 (FP32) -> A operand
+#pragma unroll 1
+            for (int o = 0; o < W; o += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float4 w0 = sm.w0b[o + 2 * e], w1 = sm.w0b[o + 2 * e + 1];
+                    const float z0 = fmaf(w0.x, px, fmaf(w0.y, py, fmaf(w0.z, pz, w0.w)));
+                    const float z1 = fmaf(w1.x, px, fmaf(w1.y, py, fmaf(w1.z, pz, w1.w)));
+                    pk[e] = pack_relu_bf16(z0, z1);
+                }
+                const int kb = o >> 6, c = (o & 63) >> 3;
+                sts128(arow + kb * (TM * 128) + ((c ^ sw) << 4), pk[0], pk[1], pk[2], pk[3]);
+            }
+            fence_async_smem();
+            mbar_arrive(&sm.a_full);
+            // 3. hidden layers
+            float gsum = 0.f;
+            for (int l = 0; l < m.n_mid; ++l) {
+                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, s.ctr);
+                pacc ^= 1u;
+                __syncwarp();  // tcgen05.ld below needs the whole warp converged
+                tc_fence_after();
+                const float *bl = m.bm + (size_t)l * W;
+                if (l + 1 < m.n_mid) {
+#pragma unroll 1
+                    for (int j = 0; j < W / 32; ++j) {
+                        float v[32];
+                        tmem_ld32(taddr + 32 * j, v);
+                        const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
+                        const int kb = j >> 1, c0 = (j & 1) * 4;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float4 b0 = __ldg(bp + 2 * c), b1 = __ldg(bp + 2 * c + 1);
+                            const uint32_t p0 = pack_relu_bf16(v[8 * c + 0] + b0.x, v[8 * c + 1] + b0.y);
+                            const uint32_t p1 = pack_relu_bf16(v[8 * c + 2] + b0.z, v[8 * c + 3] + b0.w);
+                            const uint32_t p2 = pack_relu_bf16(v[8 * c + 4] + b1.x, v[8 * c + 5] + b1.y);
+                            const uint32_t p3 = pack_relu_bf16(v[8 * c + 6] + b1.z, v[8 * c + 7] + b1.w);
+                            sts128(arow + kb * (TM * 128) + (((c0 + c) ^ sw) << 4), p0, p1, p2, p3);
+                        }
+                    }
+                    tc_fence_before();
+                    fence_async_smem();
+                    mbar_arrive(&sm.a_full);
+                } else {
+                    // output layer in FP32 from the accumulators
+#pragma unroll 1
+                    for (int j = 0; j < W / 32; ++j) {
+                        float v[32];
+                        tmem_ld32(taddr + 32 * j, v);
+                        const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
+                        const float4 *wp = reinterpret_cast<const float4 *>(m.wout + 32 * j);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float4 b = __ldg(bp + c), w = __ldg(wp + c);
+                            gsum = fmaf(w.x, fmaxf(v[4 * c + 0] + b.x, 0.f), gsum);
+                            gsum = fmaf(w.y, fmaxf(v[4 * c + 1] + b.y, 0.f), gsum);
+                            gsum = fmaf(w.z, fmaxf(v[4 * c + 2] + b.z, 0.f), gsum);
+                            gsum = fmaf(w.w, fmaxf(v[4 * c + 3] + b.w, 0.f), gsum);
+                        }
+                    }
+                    tc_fence_before();
+                }
+            }
+            // 4. f, then the hop step or the store
+            const float f = outer_f(m, px, py, pz, gsum + m.bout);
+            if (MODE == MODE_HOP) {
+                bool mark = false;
+                int step = 1;
+                if (live) {
+                    ++evals;
+                    float d = fabsf(f) - g.eps;
+                    if (!isfinite(f)) {
+                        atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                        d = 0.f;
+                    }
+                    if (d <= g.tau) {
+                        mark = true;
+                    } else {
+                        const float stp = floorf(d * g.inv_h);
+                        step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
+                    }
+                }
+                const unsigned mm = __ballot_sync(FULL, mark);
+                if (mm) {
+                    const int leader = __ffs(mm) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
+                    base = __shfl_sync(FULL, base, leader);
+                    if (mark) {
+                        const unsigned long long mi = base + __popc(mm & lt);
+                        if (mi < (unsigned long long)s.cap_marks)
+                            s.marks_raw[mi] = pack_mark(col, (uint32_t)k, rank);
+                        else
+                            atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
+                    }
+                }
+                if (live) {
+                    if (mark) {
+                        ++rank;
+                        ++k;
+                    } else {
+                        k += step;
+                    }
+                    if (k >= N) {
+                        s.colcount[col] = rank;
+                        col = NONE;
+                    }
+                }
+            } else if (live) {
+                if (MODE == MODE_VERTS) {
+                    if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                    s.vval[idx] = f;
+                } else {
+                    outv[idx] = f;
+                }
+            }
+        }
+        if (MODE == MODE_HOP) {
+            for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+            if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+        }
+    }
+    // ---- tear-down ---------------------------------------------------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+template <int W, int MODE>
+void launch_bf16(const MlpDev &m, const GridP &g, Scratch &s, const float *p, long long n, float *out, int nsm,
+                 cudaStream_t st) {
+    const size_t smem = sizeof(SmemB<W>) + 1024;
+    cudaFuncSetAttribute(k_mlp_bf16<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = nsm;
+    if (MODE == MODE_POINTS) {
+        const long long tiles = (n + NEPI - 1) / NEPI;
+        if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
+    }
+    k_mlp_bf16<W, MODE><<<grid, NTHREADS, smem, st>>>(m, g, s, p, n, out);
+}
+
+}  // namespace
+
+#define GH_BF16_W(W, ...)                                     \
+    switch (W) {                                              \
+    case 64: { constexpr int WW = 64; __VA_ARGS__; } break;   \
+    case 128: { constexpr int WW = 128; __VA_ARGS__; } break; \
+    default: { constexpr int WW = 256; __VA_ARGS__; } break;  \
+    }
+
+bool bf16_supported(int width) { return width == 64 || width == 128 || width == 256; }
+
+void launch_hop_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
+    GH_BF16_W(m.width, launch_bf16<WW, MODE_HOP>(m, g, s, nullptr, 0, nullptr, nsm, st))
+}
+
+void launch_eval_vertices_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
+    GH_BF16_W(m.width, launch_bf16<WW, MODE_VERTS>(m, g, s, nullptr, 0, nullptr, nsm, st))
+}
+
+void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
+                                 cudaStream_t st) {
+    static thread_local Counters *ctr = nullptr;
+    if (!ctr) cudaMalloc(&ctr, sizeof(Counters));
+    cudaMemsetAsync(ctr, 0, sizeof(Counters), st);
+    Scratch s{};
+    s.ctr = ctr;
+    GridP g{};
+    GH_BF16_W(m.width, launch_bf16<WW, MODE_POINTS>(m, g, s, p, n, out, nsm, st))
+}
+
 }  // namespace gh

@@ -528,12 +528,138 @@ void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStre
 }
 
 // ---------------------------------------------------------------------------
+// FP32 refinement of the BF16 path: every corner of a marked cell whose BF16
+// corner values are not all > eps or all < -eps (so whose FP32 signs could
+// differ or which may hold the surface) is re-evaluated in FP32.  Cells whose
+// values all clear eps keep their case (0 or 255) whatever the refined values
+// of shared corners, because |f_bf16 - f_fp32| <= eps / 2.
+// ---------------------------------------------------------------------------
+__global__ void k_refine_zero(Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long V = s.ctr->verts;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += (unsigned long long)gridDim.x * blockDim.x)
+        s.vflag[v] = 0;
+}
+
+__global__ void k_refine_select(GridP g, Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long M = s.ctr->marks;
+    const int N = g.N, N1 = N + 1;
+    for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
+         m += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = s.marks_csr[m];
+        const uint32_t col = mark_col(r), k = mark_k(r);
+        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+        uint32_t idx[4];
+        bool allpos = true, allneg = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
+            idx[q] = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], k);
+            const float a = s.vval[idx[q]], b = s.vval[idx[q] + 1];
+            allpos = allpos && a > g.eps && b > g.eps;
+            allneg = allneg && a < -g.eps && b < -g.eps;
+        }
+        if (!allpos && !allneg) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s.vflag[idx[q]] = 1;
+                s.vflag[idx[q] + 1] = 1;
+            }
+        }
+    }
+}
+
+__global__ void k_refine_compact(Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long V = s.ctr->verts;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); v0 < V;
+         v0 += stride) {
+        const unsigned long long v = v0 + lane;
+        const bool f = v < V && s.vflag[v];
+        const unsigned fm = __ballot_sync(FULL, f);
+        if (!fm) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&s.ctr->refine, (unsigned long long)__popc(fm));
+        base = __shfl_sync(FULL, base, 0);
+        if (f) s.rlist[base + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)v;
+    }
+}
+
+void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st) {
+    k_refine_zero<<<1024, 256, 0, st>>>(s);
+    k_refine_select<<<1024, 256, 0, st>>>(g, s);
+    k_refine_compact<<<1024, 256, 0, st>>>(s);
+}
+
+// ---------------------------------------------------------------------------
+// Calibration helpers: seeded uniform points (splitmix64, Steele, Lea and
+// Flood 2014), the positions of the lattice vertices in the vertex list, and
+// max |a - b|.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_rand_points(float *p, long long n, float lo0, float lo1, float lo2, float ext,
+                              unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const unsigned long long r = splitmix64(seed * 0x100000001B3ull + (unsigned long long)(3 * i + a));
+            const float u = (float)(r >> 40) * (1.0f / 16777216.0f);
+            p[3 * i + a] = (a == 0 ? lo0 : (a == 1 ? lo1 : lo2)) + u * ext;
+        }
+}
+
+void launch_rand_points(float *p, long long n, const float *lo, float ext, unsigned long long seed, cudaStream_t st) {
+    k_rand_points<<<1024, 256, 0, st>>>(p, n, lo[0], lo[1], lo[2], ext, seed);
+}
+
+__global__ void k_vertex_points(GridP g, Scratch s, float *p) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long V = s.ctr->verts;
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += (unsigned long long)gridDim.x * blockDim.x) {
+        float x, y, z;
+        vertex_pos(g, s.vkey[v], x, y, z);
+        p[3 * v] = x;
+        p[3 * v + 1] = y;
+        p[3 * v + 2] = z;
+    }
+}
+
+void launch_vertex_points(const GridP &g, Scratch &s, float *p, cudaStream_t st) {
+    k_vertex_points<<<1024, 256, 0, st>>>(g, s, p);
+}
+
+__global__ void k_max_abs_diff(const float *a, const float *b, long long n, unsigned int *out) {
+    float mx = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = fabsf(a[i] - b[i]);
+        mx = (d > mx || d != d) ? (d != d ? __int_as_float(0x7f800000) : d) : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+void launch_max_abs_diff(const float *a, const float *b, long long n, unsigned int *out, cudaStream_t st) {
+    k_max_abs_diff<<<512, 256, 0, st>>>(a, b, n, out);
+}
+
+// ---------------------------------------------------------------------------
 // Results: counts, statistics and the status word.
 // ---------------------------------------------------------------------------
 __global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
     const Counters c = *s.ctr;
     long long status = GH_OK;
     if (c.flags & FLAG_NONFINITE) status = GH_ERR_NONFINITE;
+    if (c.flags & FLAG_TIMEOUT) status = GH_ERR_CUDA;
     if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) status = GH_ERR_CAPACITY;
     if (c.tris > (unsigned long long)out.capacity_tris) status = GH_ERR_CAPACITY;
     if (out.cell_ids && c.cells > (unsigned long long)out.capacity_cells) status = GH_ERR_CAPACITY;
