@@ -119,6 +119,10 @@ typedef struct {
                        /* internal scratch and retry when it overflowed, and  */
                        /* return device-side errors; 0: fully asynchronous,   */
                        /* errors land in stats->status                        */
+    int32_t ray_block; /* tuning: threads per CTA of the analytic hopper      */
+                       /* (128, 256 or 512; 0 = 256)                          */
+    int32_t mlp_tiles; /* tuning: 128-row tiles per CTA of the BF16 engine    */
+                       /* (1 or 2; 0 = 2)                                     */
 } gh_options;
 
 /* Counters written by the device (all int64 so a caller may read the struct
@@ -184,14 +188,30 @@ int gh_sdb_calibrate(gh_sdb *sdb, const gh_grid *grid, int64_t n_points, uint64_
  * GH_ERR_CUDA. */
 int gh_polygonize(const gh_grid *grid, const gh_sdb *sdb, const gh_options *opts, gh_mesh *out, void *stream);
 
-/* Polygonizes B SDBs, each on its own grid, with one persistent hopping
- * launch fed by a device work queue of (SDB, column tile) items, followed by
- * batched Marching Cubes.  grids[b], sdbs[b], outs[b] as in gh_polygonize.
- * If graph != NULL the whole sequence is captured once into a CUDA graph
- * (cudaGraphExec_t written to *graph) that the caller may replay with
- * cudaGraphLaunch; the SDBs, grids and outputs are then bound to it. */
+/* Polygonizes B SDBs, each on its own grid (Algorithm 1 for every item).
+ * The ray hopping of all analytic items runs in one persistent launch, and
+ * that of all neural items of one width in one persistent launch, each fed by
+ * device work queues (every CTA walks the items in order and takes columns
+ * from the current item's queue); lattice-vertex evaluation of the neural
+ * items is batched the same way; lists and Marching Cubes run per item.
+ * grids[b], sdbs[b], outs[b] as in gh_polygonize; every item needs its own
+ * SDB object (B distinct pointers).  opts->precision applies to the neural
+ * items (analytic items always run in FP32); BF16 items use opts->eps when
+ * >= 0, else their calibrated eps.
+ * graph == NULL: runs the batch on stream (sync / async as opts->sync).
+ * graph != NULL: runs the batch once synchronously (sizing the scratch), then
+ * captures the same launch sequence into a CUDA graph and writes its
+ * cudaGraphExec_t to *graph without running it again; replay it with
+ * cudaGraphLaunch on a stream, and release it with gh_batch_graph_free.  The
+ * SDBs, grids and output buffers stay bound to the graph. */
 int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
                         gh_mesh *outs, void *stream, void **graph);
+
+/* Replays a graph made by gh_polygonize_batch on stream (cudaGraphLaunch). */
+int gh_batch_graph_launch(void *graph, void *stream);
+
+/* Destroys a graph made by gh_polygonize_batch and the descriptors it uses. */
+int gh_batch_graph_free(void *graph);
 
 /* No-allocation variant of gh_polygonize for analytic (CSG) scenes.  The
  * paper has no counterpart: this entry point serves callers that cannot

@@ -268,3 +268,86 @@ def mc_table(maxt: int = 16):
     edges = np.full((256, maxt, 3), -1, np.int32)
     mx = lib().or_mc_table(_ptr(ntri), _ptr(edges), maxt)
     return ntri, edges, int(mx)
+
+
+# ---------------------------------------------------------------------------
+# Batched FP64 evaluation of the neural SDB with numpy matrix products (the
+# same definition as oracle.c's mlp_g / mlp_grads, written layer by layer;
+# a matrix product per layer is the only library step).  Used where the C
+# loops would be too slow: finite differences over ~10^5 mesh vertices.
+# ---------------------------------------------------------------------------
+def np_layers(params, width, nmid):
+    p = np.asarray(params, np.float64).ravel()
+    W = width
+    shapes = [(W, 3)] + [(W, W)] * nmid + [(1, W)]
+    out, o = [], 0
+    for od, id_ in shapes:
+        M = p[o:o + od * id_].reshape(od, id_)
+        o += od * id_
+        b = p[o:o + od]
+        o += od
+        out.append((M, b))
+    assert o == p.size
+    return out
+
+
+def np_forward(layers, P):
+    """Pre-activations z_0..z_L of the hidden layers and g."""
+    P = np.asarray(P, np.float64).reshape(-1, 3)
+    zs = []
+    a = P
+    for W, b in layers[:-1]:
+        z = a @ W.T + b
+        zs.append(z)
+        a = np.maximum(z, 0.0)
+    Wo, bo = layers[-1]
+    g = (a @ Wo.T + bo)[:, 0]
+    return zs, g
+
+
+def np_eval(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+    """f(p) = (|p| - r0 + alpha g(p)) / beta / lam at the rows of P (Sec. 5.2)."""
+    P = np.asarray(P, np.float64).reshape(-1, 3)
+    _, g = np_forward(np_layers(params, width, nmid), P)
+    return (np.linalg.norm(P, axis=1) - r0 + alpha * g) / beta / lam
+
+
+def np_grad_x(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+    P = np.asarray(P, np.float64).reshape(-1, 3)
+    layers = np_layers(params, width, nmid)
+    zs, _ = np_forward(layers, P)
+    d = layers[-1][0][0][None, :] * (zs[-1] > 0)  # dg/dz_L
+    for l in range(len(zs) - 1, 0, -1):
+        d = (d @ layers[l][0]) * (zs[l - 1] > 0)
+    dgdp = d @ layers[0][0]
+    r = np.linalg.norm(P, axis=1, keepdims=True)
+    return (P / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
+
+
+def np_adjoint(params, width, nmid, V, dLdv, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+    """Implicit-surface adjoint sum_v s_v df/dtheta(v) with
+    s_v = -(dL/dv . grad_x f)/|grad_x f|^2, packed like the parameters."""
+    V = np.asarray(V, np.float64).reshape(-1, 3)
+    G = np.asarray(dLdv, np.float64).reshape(-1, 3)
+    layers = np_layers(params, width, nmid)
+    zs, _ = np_forward(layers, V)
+    ds = [None] * len(zs)
+    d = layers[-1][0][0][None, :] * (zs[-1] > 0)
+    ds[-1] = d
+    for l in range(len(zs) - 1, 0, -1):
+        d = (d @ layers[l][0]) * (zs[l - 1] > 0)
+        ds[l - 1] = d
+    dgdp = ds[0] @ layers[0][0]
+    r = np.linalg.norm(V, axis=1, keepdims=True)
+    gx = (V / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
+    s = -(G * gx).sum(1) / (gx * gx).sum(1)
+    c = alpha / (beta * lam)
+    out = []
+    acts = [V] + [np.maximum(z, 0.0) for z in zs]
+    for l in range(len(zs)):
+        sd = ds[l] * s[:, None]
+        out.append((sd.T @ acts[l]).ravel())
+        out.append(sd.sum(0))
+    out.append((acts[-1] * s[:, None]).sum(0))
+    out.append(np.array([s.sum()]))
+    return c * np.concatenate(out)

@@ -1,0 +1,38 @@
+"""torch.autograd binding of the implicit-surface adjoint.
+
+``polygonize_mlp(params, ...)`` returns the deduplicated mesh vertices of the
+neural SDB with parameters ``params`` (a float32 tensor packed like the MLP
+blob) and its faces; gradients of any loss on the vertices flow back to
+``params`` through gh_backward: for a vertex on the level set f = 0,
+dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gh
+
+
+class _ImplicitPolygonize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, params, width, n_mid, N, lo, hi, r0, alpha, beta, lam, precision):
+        sdb = gh.MlpSdb(params.detach().cpu().numpy(), width, n_mid, r0, alpha, beta, lam)
+        eps = sdb.calibrate(N, lo, hi) if precision == "bf16" else None
+        mesh = gh.polygonize(sdb, N, lo=lo, hi=hi, precision=precision, keys=True, eps=eps)
+        verts, faces, _ = gh.unique_vertices(mesh)
+        ctx.sdb = sdb
+        ctx.save_for_backward(verts)
+        ctx.mark_non_differentiable(faces)
+        return verts, faces
+
+    @staticmethod
+    def backward(ctx, dverts, dfaces):
+        (verts,) = ctx.saved_tensors
+        grad = gh.backward(ctx.sdb, verts, dverts)
+        return (grad.to(dverts.device),) + (None,) * 10
+
+
+def polygonize_mlp(params, width, n_mid=5, N=256, lo=-1.0, hi=1.0, r0=0.6, alpha=0.1, beta=1.1, lam=1.0,
+                   precision="fp32"):
+    """(verts [V,3], faces [T,3]) of the neural SDB; differentiable in params."""
+    return _ImplicitPolygonize.apply(params, width, n_mid, N, lo, hi, r0, alpha, beta, lam, precision)

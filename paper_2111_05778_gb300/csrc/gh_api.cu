@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -219,6 +220,11 @@ struct gh_sdb {
     // scratch, grown on demand
     Scratch scr{};
     int scr_N = 0;
+    float *adj = nullptr;  // adjoint work buffer
+    size_t adj_floats = 0;
+    Item h_item{};           // descriptor of the last single call (host copy)
+    Item *d_item = nullptr;  // and on the device
+    bool item_valid = false;
     std::mutex mu;
 };
 
@@ -322,12 +328,16 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
                 }
         }
     }
-    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout;
+    std::vector<float> wmid((size_t)h.n_mid * W * W);
+    for (int l = 0; l < h.n_mid; ++l)
+        memcpy(wmid.data() + (size_t)l * W * W, mid + (size_t)l * ((size_t)W * W + W), sizeof(float) * W * W);
+    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout, *d_wmid;
     uint16_t *d_wbf;
     if (dev_alloc(s, &d_w0, 3 * W) || dev_alloc(s, &d_b0, W) || dev_alloc(s, &d_wt, wt.size()) ||
         dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np) ||
-        dev_alloc(s, &d_wbf, wbf.size()))
+        dev_alloc(s, &d_wbf, wbf.size()) || dev_alloc(s, &d_wmid, wmid.size()))
         return GH_ERR_CUDA;
+    GH_CUDA(cudaMemcpy(d_wmid, wmid.data(), sizeof(float) * wmid.size(), cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_wbf, wbf.data(), sizeof(uint16_t) * wbf.size(), cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_w0, W0, sizeof(float) * 3 * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_b0, B0, sizeof(float) * W, cudaMemcpyHostToDevice));
@@ -349,6 +359,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.wout = d_wout;
     m.bout = wout[W];
     m.wbf = d_wbf;
+    m.wmid = d_wmid;
     s->nparam = np;
     return GH_OK;
 }
@@ -392,6 +403,8 @@ static void free_scratch(gh_sdb *s) {
 extern "C" int gh_destroy_sdb(gh_sdb *s) {
     if (!s) return GH_OK;
     free_scratch(s);
+    if (s->adj) cudaFree(s->adj);
+    if (s->d_item) cudaFree(s->d_item);
     for (void *p : s->dbufs) cudaFree(p);
     delete s;
     return GH_OK;
@@ -422,6 +435,30 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     c.cap_marks = cm;
     c.cap_verts = cv;
     s->scr_N = NN;
+    return GH_OK;
+}
+
+static Item make_item(const gh_sdb *s, const GridP &g) {
+    Item it{};  // zero-initialised, padding included, so descriptors compare bytewise
+    it.g = g;
+    it.s = s->scr;
+    it.m = s->mlp;
+    it.prims = s->d_prims;
+    it.nprim = s->nprim;
+    it.kind = s->kind;
+    return it;
+}
+
+// Uploads the SDB's single-call descriptor when it changed.
+static int sync_item(gh_sdb *s, const GridP &g, cudaStream_t st) {
+    const Item it = make_item(s, g);
+    if (!s->d_item) GH_CUDA(cudaMalloc((void **)&s->d_item, sizeof(Item)));
+    if (!s->item_valid || memcmp(&it, &s->h_item, sizeof(Item)) != 0) {
+        s->h_item = it;
+        GH_CUDA(cudaMemcpyAsync(s->d_item, &s->h_item, sizeof(Item), cudaMemcpyHostToDevice, st));
+        GH_CUDA(cudaStreamSynchronize(st));
+        s->item_valid = true;
+    }
     return GH_OK;
 }
 
@@ -501,36 +538,40 @@ static inline void mark_phase(int i, cudaStream_t st) {
 static constexpr int LAUNCHES_HOP = 2, LAUNCHES_LISTS = 8, LAUNCHES_VERTS = 1, LAUNCHES_REFINE = 4,
                      LAUNCHES_MC = 2;
 
-static int enqueue_once(gh_sdb *s, const GridP &g, int precision, const gh_mesh &out, int nsm, cudaStream_t st) {
+static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh_mesh &out, int nsm,
+                        cudaStream_t st) {
     Scratch &c = s->scr;
+    int rc = sync_item(s, g, st);
+    if (rc) return rc;
     long long launches = LAUNCHES_HOP + LAUNCHES_LISTS + LAUNCHES_VERTS + LAUNCHES_MC;
+    const int tiles = o.mlp_tiles == 1 ? 1 : 2;
     mark_phase(0, st);
     launch_init(c, st);
     if (s->kind == GH_SDB_CSG) {
-        launch_hop_csg(s->d_prims, s->nprim, g, c, nsm, st);
+        launch_hop_csg(s->d_item, 1, s->nprim, nsm, o.ray_block, st);
         mark_phase(1, st);
         launch_build_lists(g, c, st);
         mark_phase(2, st);
         launch_eval_vertices_csg(s->d_prims, s->nprim, g, c, nsm, st);
         mark_phase(3, st);
         mark_phase(4, st);
-    } else if (precision == GH_FP32) {
-        launch_hop_mlp_fp32(s->mlp, g, c, nsm, st);
+    } else if (o.precision == GH_FP32) {
+        launch_hop_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, st);
         mark_phase(1, st);
         launch_build_lists(g, c, st);
         mark_phase(2, st);
-        launch_eval_vertices_mlp_fp32(s->mlp, g, c, nsm, false, st);
+        launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, false, st);
         mark_phase(3, st);
         mark_phase(4, st);
     } else {
-        launch_hop_mlp_bf16(s->mlp, g, c, nsm, st);
+        launch_hop_mlp_bf16(s->d_item, 1, s->mlp.width, nsm, tiles, st);
         mark_phase(1, st);
         launch_build_lists(g, c, st);
         mark_phase(2, st);
-        launch_eval_vertices_mlp_bf16(s->mlp, g, c, nsm, st);
+        launch_eval_vertices_mlp_bf16(s->d_item, 1, s->mlp.width, nsm, tiles, st);
         mark_phase(3, st);
         launch_refine_select(g, c, st);
-        launch_eval_vertices_mlp_fp32(s->mlp, g, c, nsm, true, st);
+        launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, true, st);
         mark_phase(4, st);
         launches += LAUNCHES_REFINE;
     }
@@ -547,7 +588,7 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
                              void *stream) {
     gh_sdb *s = const_cast<gh_sdb *>(csdb);
     if (!s) return fail(GH_ERR_ARG, "NULL sdb");
-    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1};
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0};
     if (opts) o = *opts;
     GridP g;
     int rc = check_grid(grid, &g, o.tau_mode);
@@ -573,7 +614,7 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
     long long want_v = 2 * want_m;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = ensure_scratch(s, g.N, want_m, want_v))) return rc;
-        if ((rc = enqueue_once(s, g, o.precision, *out, nsm, st))) return rc;
+        if ((rc = enqueue_once(s, g, o, *out, nsm, st))) return rc;
         if (!o.sync) return GH_OK;
         Counters c;
         GH_CUDA(cudaMemcpyAsync(&c, s->scr.ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -653,8 +694,9 @@ extern "C" int gh_sdb_calibrate(gh_sdb *s, const gh_grid *grid, int64_t n_points
     if ((rc = ensure_scratch(s, gc.N, 8 * N2 > (1 << 16) ? 8 * N2 : (1 << 16), 16 * N2 > (1 << 17) ? 16 * N2 : (1 << 17))))
         return rc;
     Scratch &c = s->scr;
+    if ((rc = sync_item(s, gc, st))) return rc;
     launch_init(c, st);
-    launch_hop_mlp_fp32(s->mlp, gc, c, nsm, st);
+    launch_hop_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, st);
     launch_build_lists(gc, c, st);
     Counters hc;
     GH_CUDA(cudaMemcpyAsync(&hc, c.ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -694,16 +736,266 @@ extern "C" int gh_sdb_calibrate(gh_sdb *s, const gh_grid *grid, int64_t n_points
     return GH_OK;
 }
 
-extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
-                                   gh_mesh *outs, void *stream, void **graph) {
-    (void)B; (void)grids; (void)sdbs; (void)opts; (void)outs; (void)stream; (void)graph;
-    return fail(GH_ERR_UNIMPLEMENTED, "gh_polygonize_batch: not available yet");
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    std::vector<int> order;          // items grouped: analytic first, then neural by (width, depth), N descending
+    std::vector<std::pair<int, int>> groups;  // [begin, end) into order
+    std::vector<GridP> g;            // per item (original index)
+    Item *d_items = nullptr;         // device descriptors in `order`
+};
+
+static std::mutex g_graph_mu;
+static std::vector<std::pair<void *, Item *>> g_graph_items;
+
+static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_options &o, const gh_mesh *outs,
+                         int nsm, cudaStream_t st) {
+    const int tiles = o.mlp_tiles == 1 ? 1 : 2;
+    for (int b = 0; b < B; ++b) launch_init(sd[b]->scr, st);
+    for (auto &gr : P.groups) {
+        const gh_sdb *first = sd[P.order[gr.first]];
+        const Item *di = P.d_items + gr.first;
+        const int n = gr.second - gr.first;
+        if (first->kind == GH_SDB_CSG) {
+            int mx = 1;
+            for (int q = gr.first; q < gr.second; ++q) mx = sd[P.order[q]]->nprim > mx ? sd[P.order[q]]->nprim : mx;
+            launch_hop_csg(di, n, mx, nsm, o.ray_block, st);
+        } else if (o.precision == GH_FP32) {
+            launch_hop_mlp_fp32(di, n, first->mlp.width, nsm, st);
+        } else {
+            launch_hop_mlp_bf16(di, n, first->mlp.width, nsm, tiles, st);
+        }
+    }
+    for (int b = 0; b < B; ++b) launch_build_lists(P.g[b], sd[b]->scr, st);
+    for (auto &gr : P.groups) {
+        const gh_sdb *first = sd[P.order[gr.first]];
+        const Item *di = P.d_items + gr.first;
+        const int n = gr.second - gr.first;
+        if (first->kind == GH_SDB_CSG) {
+            for (int q = gr.first; q < gr.second; ++q) {
+                const int b = P.order[q];
+                launch_eval_vertices_csg(sd[b]->d_prims, sd[b]->nprim, P.g[b], sd[b]->scr, nsm, st);
+            }
+        } else if (o.precision == GH_FP32) {
+            launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, false, st);
+        } else {
+            launch_eval_vertices_mlp_bf16(di, n, first->mlp.width, nsm, tiles, st);
+            for (int q = gr.first; q < gr.second; ++q) {
+                const int b = P.order[q];
+                launch_refine_select(P.g[b], sd[b]->scr, st);
+            }
+            launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, true, st);
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        launch_mc(P.g[b], sd[b]->scr, outs[b], nsm, st);
+        launch_finalize(sd[b]->scr, outs[b], (long long)P.g[b].N * P.g[b].N, st);
+    }
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
 }
 
-extern "C" int gh_backward(const gh_sdb *s, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
+extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
+                                   gh_mesh *outs, void *stream, void **graph) {
+    if (B < 1 || !grids || !sdbs || !outs) return fail(GH_ERR_ARG, "gh_polygonize_batch: empty or NULL arguments");
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0};
+    if (opts) o = *opts;
+    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
+        return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
+    int dev, nsm, rc;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    std::vector<gh_sdb *> sd(B);
+    BatchPlan P;
+    P.g.resize(B);
+    for (int b = 0; b < B; ++b) {
+        sd[b] = const_cast<gh_sdb *>(sdbs[b]);
+        if (!sd[b]) return fail(GH_ERR_ARG, "item %d: NULL sdb", b);
+        for (int q = 0; q < b; ++q)
+            if (sd[q] == sd[b]) return fail(GH_ERR_ARG, "items %d and %d share one SDB object", q, b);
+        if (sd[b]->device != dev) return fail(GH_ERR_ARG, "item %d: SDB on another device", b);
+        if ((rc = check_grid(&grids[b], &P.g[b], o.tau_mode))) return rc;
+        if ((rc = check_mesh(&outs[b]))) return rc;
+        if (sd[b]->kind == GH_SDB_MLP && o.precision == GH_BF16_REFINE) {
+            const float eps = o.eps >= 0.f ? o.eps : sd[b]->eps;
+            if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "item %d: BF16 needs eps (calibrate the SDB)", b);
+            P.g[b].eps = eps;
+        }
+    }
+    // groups: analytic items, then neural items by (width, depth); N descending inside a group
+    std::vector<int> idx(B);
+    for (int b = 0; b < B; ++b) idx[b] = b;
+    auto key = [&](int b) {
+        const gh_sdb *x = sd[b];
+        return x->kind == GH_SDB_CSG ? 0 : 1 + x->mlp.width * 64 + x->mlp.n_mid;
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        if (key(a) != key(b)) return key(a) < key(b);
+        return P.g[a].N > P.g[b].N;
+    });
+    P.order = idx;
+    for (int q = 0; q < B;) {
+        int e = q;
+        while (e < B && key(idx[e]) == key(idx[q])) ++e;
+        P.groups.push_back({q, e});
+        q = e;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (int b = 0; b < B; ++b) locks.emplace_back(sd[b]->mu);
+    std::vector<long long> want_m(B), want_v(B);
+    for (int b = 0; b < B; ++b) {
+        const long long N2 = (long long)P.g[b].N * P.g[b].N;
+        want_m[b] = 8 * N2 > (1 << 16) ? 8 * N2 : (1 << 16);
+        want_v[b] = 2 * want_m[b];
+    }
+    Item *d_items = nullptr;
+    GH_CUDA(cudaMalloc((void **)&d_items, sizeof(Item) * B));
+    P.d_items = d_items;
+    std::vector<Item> h_items(B);
+    const bool sync = o.sync || graph;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        for (int b = 0; b < B; ++b)
+            if ((rc = ensure_scratch(sd[b], P.g[b].N, want_m[b], want_v[b]))) {
+                cudaFree(d_items);
+                return rc;
+            }
+        for (int q = 0; q < B; ++q) h_items[q] = make_item(sd[P.order[q]], P.g[P.order[q]]);
+        GH_CUDA(cudaMemcpyAsync(d_items, h_items.data(), sizeof(Item) * B, cudaMemcpyHostToDevice, st));
+        if ((rc = batch_enqueue(P, B, sd.data(), o, outs, nsm, st))) {
+            cudaFree(d_items);
+            return rc;
+        }
+        if (!sync) break;  // asynchronous: d_items must outlive the work; keep it with the last batch
+        GH_CUDA(cudaStreamSynchronize(st));
+        bool grow = false;
+        for (int b = 0; b < B; ++b) {
+            Counters c;
+            GH_CUDA(cudaMemcpy(&c, sd[b]->scr.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+            if (c.flags & FLAG_TIMEOUT) {
+                cudaFree(d_items);
+                return fail(GH_ERR_CUDA, "item %d: a bounded device wait timed out", b);
+            }
+            if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) {
+                if (c.flags & FLAG_MARK_OVERFLOW) want_m[b] = (long long)(c.marks + c.marks / 4 + 1024);
+                want_v[b] = (c.flags & FLAG_VERT_OVERFLOW) ? (long long)(c.verts + c.verts / 4 + 1024) : 2 * want_m[b];
+                if (want_v[b] < 2 * want_m[b]) want_v[b] = 2 * want_m[b];
+                grow = true;
+            }
+        }
+        if (grow) continue;
+        rc = GH_OK;
+        for (int b = 0; b < B && rc == GH_OK; ++b) {
+            Counters c;
+            GH_CUDA(cudaMemcpy(&c, sd[b]->scr.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+            if (c.flags & FLAG_NONFINITE) rc = fail(GH_ERR_NONFINITE, "item %d: NaN or inf", b);
+            else if (c.tris > (unsigned long long)outs[b].capacity_tris)
+                rc = fail(GH_ERR_CAPACITY, "item %d: triangle buffer holds %lld, %llu needed", b,
+                          (long long)outs[b].capacity_tris, c.tris);
+            else if (outs[b].cell_ids && c.cells > (unsigned long long)outs[b].capacity_cells)
+                rc = fail(GH_ERR_CAPACITY, "item %d: cell buffer too small", b);
+        }
+        if (rc || !graph) {
+            cudaFree(d_items);
+            return rc;
+        }
+        // capture the same sequence into a graph bound to these buffers
+        cudaGraph_t gr = nullptr;
+        GH_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const int erc = batch_enqueue(P, B, sd.data(), o, outs, nsm, st);
+        const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+        if (erc || ec != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaFree(d_items);
+            return erc ? erc : fail(GH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) {
+            cudaFree(d_items);
+            return fail(GH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            g_graph_items.push_back({(void *)ex, d_items});
+        }
+        *graph = (void *)ex;
+        return GH_OK;
+    }
+    if (!sync) {
+        // the descriptors must live until the stream has consumed them
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        g_graph_items.push_back({nullptr, d_items});
+        return GH_OK;
+    }
+    cudaFree(d_items);
+    return fail(GH_ERR_CAPACITY, "internal scratch kept overflowing");
+}
+
+extern "C" int gh_batch_graph_launch(void *graph, void *stream) {
+    if (!graph) return fail(GH_ERR_ARG, "gh_batch_graph_launch: NULL graph");
+    GH_CUDA(cudaGraphLaunch((cudaGraphExec_t)graph, (cudaStream_t)stream));
+    return GH_OK;
+}
+
+extern "C" int gh_batch_graph_free(void *graph) {
+    if (!graph) return GH_OK;
+    Item *items = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (size_t i = 0; i < g_graph_items.size(); ++i)
+            if (g_graph_items[i].first == graph) {
+                items = g_graph_items[i].second;
+                g_graph_items.erase(g_graph_items.begin() + i);
+                break;
+            }
+    }
+    GH_CUDA(cudaGraphExecDestroy((cudaGraphExec_t)graph));
+    if (items) cudaFree(items);
+    return GH_OK;
+}
+
+extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
                            void *stream) {
-    (void)s; (void)verts; (void)dL_dv; (void)V; (void)dL_dtheta; (void)stream;
-    return fail(GH_ERR_UNIMPLEMENTED, "gh_backward: not available yet");
+    gh_sdb *s = const_cast<gh_sdb *>(cs);
+    if (!s || s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "gh_backward needs a neural SDB");
+    if (V < 0 || V > (1ll << 31) - 1) return fail(GH_ERR_ARG, "gh_backward: V = %lld out of range", (long long)V);
+    if (!dL_dtheta || (V > 0 && (!verts || !dL_dv))) return fail(GH_ERR_ARG, "gh_backward: NULL pointer");
+    int dev, nsm, rc;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (V == 0) {
+        GH_CUDA(cudaMemsetAsync(dL_dtheta, 0, sizeof(float) * s->nparam, st));
+        return GH_OK;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int W = s->mlp.width, L = s->mlp.n_mid, S = 64;
+    const int VC = V < 65536 ? (int)V : 65536;
+    const size_t need = adjoint_buffer_floats(W, L, 65536, S);
+    if (s->adj_floats < need) {
+        if (s->adj) cudaFree(s->adj);
+        s->adj = nullptr;
+        s->adj_floats = 0;
+        GH_CUDA(cudaMalloc((void **)&s->adj, sizeof(float) * need));
+        s->adj_floats = need;
+    }
+    AdjBuffers b;
+    b.VC = 65536;
+    b.splits = S;
+    b.Z = s->adj;
+    b.D = b.Z + (size_t)(L + 1) * b.VC * W;
+    b.s = b.D + (size_t)(L + 1) * b.VC * W;
+    b.part = b.s + b.VC;
+    b.ones = b.part + (size_t)S * W * W;
+    adjoint_fill_ones(b.ones, b.VC, st);
+    (void)VC;
+    for (long long v0 = 0; v0 < V; v0 += b.VC) {
+        const int n = (int)((V - v0) < b.VC ? (V - v0) : b.VC);
+        adjoint_chunk(s->mlp, verts + 3 * v0, dL_dv + 3 * v0, n, dL_dtheta, v0 > 0, b, st);
+    }
+    GH_CUDA(cudaGetLastError());
+    return GH_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -713,6 +1005,8 @@ extern "C" int gh_backward(const gh_sdb *s, const float *verts, const float *dL_
 // stand-in); the device address is looked up once per device below.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GH_NOALLOC_SCRATCH_BYTES];
+static __device__ Item g_noalloc_item;  // descriptor of the call (static, like the scratch)
+static void *g_noalloc_item_addr[64];
 static void *g_noalloc_addr[64];
 static std::mutex g_noalloc_mu;
 
@@ -741,9 +1035,15 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
             if (e != cudaSuccess || !p)
                 return fail(GH_ERR_CUDA, "cudaGetSymbolAddress(no-allocation scratch): %s", cudaGetErrorString(e));
             g_noalloc_addr[dev] = p;
+            void *pi = nullptr;
+            const cudaError_t e2 = cudaGetSymbolAddress(&pi, g_noalloc_item);
+            if (e2 != cudaSuccess || !pi)
+                return fail(GH_ERR_CUDA, "cudaGetSymbolAddress(no-allocation descriptor): %s", cudaGetErrorString(e2));
+            g_noalloc_item_addr[dev] = pi;
         }
         base = g_noalloc_addr[dev];
     }
+    Item *ditem = (Item *)g_noalloc_item_addr[dev];
     // carve the array for the largest grid it accepts
     const size_t NN = GH_NOALLOC_MAX_N, ncols = NN * NN, nlines = (NN + 1) * (NN + 1);
     char *q = (char *)base;
@@ -776,8 +1076,15 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     if (off > GH_NOALLOC_SCRATCH_BYTES) return fail(GH_ERR_CUDA, "no-allocation scratch layout overflows");
     cudaStream_t st = (cudaStream_t)stream;
     const Prim *dp = reinterpret_cast<const Prim *>(prims);
+    Item hitem{};
+    hitem.g = g;
+    hitem.s = c;
+    hitem.prims = dp;
+    hitem.nprim = n_prim;
+    hitem.kind = GH_SDB_CSG;
+    GH_CUDA(cudaMemcpyAsync(ditem, &hitem, sizeof(Item), cudaMemcpyHostToDevice, st));
     launch_init(c, st);  // clears the counters left by the previous call
-    launch_hop_csg(dp, n_prim, g, c, nsm, st);
+    launch_hop_csg(ditem, 1, n_prim, nsm, 256, st);
     launch_build_lists(g, c, st);
     launch_eval_vertices_csg(dp, n_prim, g, c, nsm, st);
     launch_mc(g, c, *out, nsm, st);

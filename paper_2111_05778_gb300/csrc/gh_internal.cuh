@@ -63,6 +63,7 @@ struct MlpDev {
     const float *wout;  // [W]
     float bout;
     const uint16_t *wbf;  // n_mid x BF16 hidden weights in the tensor-core tile layout
+    const float *wmid;    // n_mid x [W(out)][W(in)] FP32 hidden weights, row-major
 };
 
 // Scratch of one polygonization (device pointers) and its capacities.
@@ -82,6 +83,17 @@ struct Scratch {
     long long cap_marks, cap_verts;
 };
 
+// One polygonization of a batch: grid, scratch and SDB.  Kernels that serve
+// batches walk an array of these; a single call is a batch of one.
+struct Item {
+    GridP g;
+    Scratch s;
+    MlpDev m;           // neural SDB (kind 1)
+    const Prim *prims;  // analytic SDB (kind 0)
+    int nprim;
+    int kind;
+};
+
 // Packing of mark records.
 __host__ __device__ inline unsigned long long pack_mark(uint32_t col, uint32_t k, uint32_t rank) {
     return (unsigned long long)col | ((unsigned long long)k << 24) | ((unsigned long long)rank << 40);
@@ -93,7 +105,7 @@ __host__ __device__ inline uint32_t mark_rank(unsigned long long m) { return (ui
 // ---- launchers implemented in the kernels' translation units ----------------
 cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges);  // k_pipeline.cu
 void launch_init(Scratch &s, cudaStream_t st);
-void launch_hop_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_hop_csg(const Item *items, int n_items, int max_prims, int nsm, int block, cudaStream_t st);
 void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,
                               cudaStream_t st);
@@ -103,19 +115,29 @@ void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long l
                             cudaStream_t st);
 
 // neural SDB, FP32 on the FFMA pipe (k_mlp_fp32.cu)
-void launch_hop_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
-void launch_eval_vertices_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, bool refine_list,
+void launch_hop_mlp_fp32(const Item *items, int n_items, int width, int nsm, cudaStream_t st);
+void launch_eval_vertices_mlp_fp32(const Item *items, int n_items, int width, int nsm, bool refine_list,
                                    cudaStream_t st);
 void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
 
 // neural SDB, BF16 on tcgen05 tensor cores (k_mlp_bf16.cu)
 bool bf16_supported(int width);
-void launch_hop_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
-void launch_eval_vertices_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st);
+void launch_hop_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st);
+void launch_eval_vertices_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st);
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
 void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);  // k_pipeline.cu
+
+// implicit-surface adjoint (k_adjoint.cu)
+struct AdjBuffers {
+    float *Z, *D, *s, *part, *ones;
+    int VC, splits;
+};
+size_t adjoint_buffer_floats(int W, int n_mid, int VC, int splits);
+void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, float *grad, bool accumulate,
+                   const AdjBuffers &b, cudaStream_t st);
+void adjoint_fill_ones(float *p, long long n, cudaStream_t st);
 
 // calibration helpers (k_pipeline.cu)
 void launch_rand_points(float *p, long long n, const float *lo, float ext, unsigned long long seed, cudaStream_t st);

@@ -1,0 +1,241 @@
+// Implicit-surface adjoint of a neural SDB (gh_backward).
+//
+// A mesh vertex v that stays on the level set f(v; theta) = 0 moves with the
+// parameters as dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2, so a loss on
+// the vertices has
+//   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f(v)) / |grad_x f(v)|^2.
+// For f = (|p| - r0 + alpha g(p)) / (beta lambda) and g a ReLU MLP
+//   z_0 = W_0 p + b_0, z_l = W_l relu(z_{l-1}) + b_l (l = 1..L), g = w . relu(z_L) + b,
+// back-propagation gives delta_L = w * [z_L > 0], delta_{l-1} = (W_l^T delta_l) *
+// [z_{l-1} > 0], dg/dp = W_0^T delta_0, and with c = alpha / (beta lambda)
+//   dL/dW_l = c sum_v s_v delta_l relu(z_{l-1})^T,  dL/db_l = c sum_v s_v delta_l,
+//   dL/dW_0 = c sum_v s_v delta_0 p^T,  dL/dw = c sum_v s_v relu(z_L),  dL/db = c sum_v s_v.
+// The activations are recomputed from the vertices (nothing is kept from the
+// polygonization).  Over a chunk of vertices every step is a dense FP32
+// product on the FFMA pipe (k_gemm, 128 x 128 tiles, 8 x 8 per thread); the
+// sums over vertices use a split over the vertex axis whose partial results
+// are added in a fixed order, so the gradient is deterministic.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "gh_internal.cuh"
+
+namespace gh {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8, GT = 256;
+
+// C[M x N] (+ split z: C + z*M*ldc) = sum_k opA(m,k) opB(k,n) over the k-range
+// [z*kchunk, (z+1)*kchunk) with opA(m,k) = (TA ? A[k*lda+m] : A[m*lda+k]),
+// relu'd if RA and scaled by ksc[k]; opB likewise.  Epilogue: + bias[n],
+// then * [mask[m*ldc+n] > 0].
+template <bool TA, bool TB, bool RA, bool RB>
+__global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *__restrict__ A, int lda,
+                                             const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                                             const float *__restrict__ bias, const float *__restrict__ mask,
+                                             const float *__restrict__ ksc, int kchunk) {
+    __shared__ __align__(16) float As[BK][BM];
+    __shared__ __align__(16) float Bs[BK][BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        // stage 128 x 8 of A and 8 x 128 of B (4 elements per thread each)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * GT;  // 0..1023
+            {
+                const int mm = TA ? (e & (BM - 1)) : (e >> 3), kk = TA ? (e >> 7) : (e & 7);
+                const int m = m0 + mm, k = k0 + kk;
+                float v = 0.f;
+                if (m < M && k < ke) {
+                    v = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+                    if (RA) v = fmaxf(v, 0.f);
+                    if (ksc) v *= ksc[k];
+                }
+                As[kk][mm] = v;
+            }
+            {
+                const int nn = TB ? (e >> 3) : (e & (BN - 1)), kk = TB ? (e & 7) : (e >> 7);
+                const int n = n0 + nn, k = k0 + kk;
+                float v = 0.f;
+                if (n < N && k < ke) {
+                    v = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+                    if (RB) v = fmaxf(v, 0.f);
+                }
+                Bs[kk][nn] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[8], b[8];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 8 + 4]);
+            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float *Cz = C + (size_t)blockIdx.z * M * ldc;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + ty * 8 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = n0 + tx * 8 + j;
+            if (n >= N) continue;
+            float v = acc[i][j];
+            if (bias) v += bias[n];
+            if (mask && !(mask[(size_t)m * ldc + n] > 0.f)) v = 0.f;
+            Cz[(size_t)m * ldc + n] = v;
+        }
+    }
+}
+
+template <bool TA, bool TB, bool RA, bool RB>
+void gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc, const float *bias,
+          const float *mask, const float *ksc, int splits, cudaStream_t st) {
+    const int kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    k_gemm<TA, TB, RA, RB><<<grid, GT, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ksc, kchunk);
+}
+
+// z_0 = W_0 p + b_0 for a chunk of vertices
+__global__ void k_adj_in(const float *__restrict__ P, int V, const float *__restrict__ w0, const float *__restrict__ b0,
+                         int W, float *__restrict__ Z0) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)V * W;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(e / W), o = (int)(e - (long long)v * W);
+        Z0[e] = fmaf(w0[3 * o], P[3 * v], fmaf(w0[3 * o + 1], P[3 * v + 1], fmaf(w0[3 * o + 2], P[3 * v + 2], b0[o])));
+    }
+}
+
+// delta_L = w * [z_L > 0]
+__global__ void k_adj_top(const float *__restrict__ ZL, int V, const float *__restrict__ wout, int W,
+                          float *__restrict__ D) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)V * W;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(e % W);
+        D[e] = ZL[e] > 0.f ? wout[o] : 0.f;
+    }
+}
+
+// grad_x f from delta_0, then s_v
+__global__ void k_adj_s(const float *__restrict__ P, const float *__restrict__ dL, int V,
+                        const float *__restrict__ D0, const float *__restrict__ w0, int W, float alpha, float inv_bl,
+                        float *__restrict__ s) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int v = warp; v < V; v += nw) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int o = lane; o < W; o += 32) {
+            const float d = D0[(size_t)v * W + o];
+            gx = fmaf(w0[3 * o], d, gx);
+            gy = fmaf(w0[3 * o + 1], d, gy);
+            gz = fmaf(w0[3 * o + 2], d, gz);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            gx += __shfl_xor_sync(0xFFFFFFFFu, gx, off);
+            gy += __shfl_xor_sync(0xFFFFFFFFu, gy, off);
+            gz += __shfl_xor_sync(0xFFFFFFFFu, gz, off);
+        }
+        if (lane == 0) {
+            const float px = P[3 * v], py = P[3 * v + 1], pz = P[3 * v + 2];
+            const float r = sqrtf(px * px + py * py + pz * pz);
+            const float ir = r > 0.f ? 1.f / r : 0.f;
+            const float fx = (px * ir + alpha * gx) * inv_bl;
+            const float fy = (py * ir + alpha * gy) * inv_bl;
+            const float fz = (pz * ir + alpha * gz) * inv_bl;
+            const float n2 = fx * fx + fy * fy + fz * fz;
+            const float dot = dL[3 * v] * fx + dL[3 * v + 1] * fy + dL[3 * v + 2] * fz;
+            s[v] = n2 > 0.f ? -dot / n2 : 0.f;
+        }
+    }
+}
+
+// out[i] (+)= c * sum_z part[z][i], z in increasing order
+__global__ void k_adj_reduce(const float *__restrict__ part, int splits, long long n, float c, float *__restrict__ out,
+                             int accumulate) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n + i];
+        out[i] = accumulate ? out[i] + c * acc : c * acc;
+    }
+}
+
+__global__ void k_fill(float *p, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+size_t adjoint_buffer_floats(int W, int n_mid, int VC, int splits) {
+    const size_t L1 = (size_t)n_mid + 1;
+    return L1 * VC * W * 2 + VC + (size_t)splits * W * W + VC;
+}
+
+// One chunk of vertices; accumulates into grad (packed like the parameters).
+void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, float *grad, bool accumulate,
+                   const AdjBuffers &b, cudaStream_t st) {
+    const int W = m.width, L = m.n_mid, S = b.splits;
+    const float c = m.alpha / m.beta * m.inv_lam;
+    float *Zl[17], *Dl[17];
+    for (int l = 0; l <= L; ++l) {
+        Zl[l] = b.Z + (size_t)l * b.VC * W;
+        Dl[l] = b.D + (size_t)l * b.VC * W;
+    }
+    const int eb = 1024;
+    // forward: pre-activations of every layer
+    k_adj_in<<<eb, 256, 0, st>>>(P, V, m.w0, m.b0, W, Zl[0]);
+    for (int l = 1; l <= L; ++l)
+        gemm<false, true, true, false>(V, W, W, Zl[l - 1], W, m.wmid + (size_t)(l - 1) * W * W, W, Zl[l], W,
+                                       m.bm + (size_t)(l - 1) * W, nullptr, nullptr, 1, st);
+    // backward chain of g
+    k_adj_top<<<eb, 256, 0, st>>>(Zl[L], V, m.wout, W, Dl[L]);
+    for (int l = L; l >= 1; --l)
+        gemm<false, false, false, false>(V, W, W, Dl[l], W, m.wmid + (size_t)(l - 1) * W * W, W, Dl[l - 1], W,
+                                         nullptr, Zl[l - 1], nullptr, 1, st);
+    k_adj_s<<<(V + 7) / 8, 256, 0, st>>>(P, dL, V, Dl[0], m.w0, W, m.alpha, 1.f / m.beta * m.inv_lam, b.s);
+    // parameter gradients: sums over the vertices of the chunk
+    const size_t oW0 = 0, ob0 = (size_t)3 * W, omid = ob0 + W;
+    const size_t ow = omid + (size_t)L * ((size_t)W * W + W);
+    const int gb = 512;
+    // W_0 and b_0
+    gemm<true, false, false, false>(W, 3, V, Dl[0], W, P, 3, b.part, 3, nullptr, nullptr, b.s, S, st);
+    k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W * 3, c, grad + oW0, accumulate);
+    gemm<true, false, false, false>(W, 1, V, Dl[0], W, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+    k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ob0, accumulate);
+    for (int l = 1; l <= L; ++l) {
+        const size_t oW = omid + (size_t)(l - 1) * ((size_t)W * W + W), ob = oW + (size_t)W * W;
+        gemm<true, false, false, true>(W, W, V, Dl[l], W, Zl[l - 1], W, b.part, W, nullptr, nullptr, b.s, S, st);
+        k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W * W, c, grad + oW, accumulate);
+        gemm<true, false, false, false>(W, 1, V, Dl[l], W, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+        k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ob, accumulate);
+    }
+    // output layer
+    gemm<false, false, false, true>(1, W, V, b.ones, V, Zl[L], W, b.part, W, nullptr, nullptr, b.s, S, st);
+    k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ow, accumulate);
+    gemm<false, false, false, false>(1, 1, V, b.ones, V, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+    k_adj_reduce<<<1, 32, 0, st>>>(b.part, S, 1, c, grad + ow + W, accumulate);
+}
+
+void adjoint_fill_ones(float *p, long long n, cudaStream_t st) { k_fill<<<256, 256, 0, st>>>(p, n, 1.f); }
+
+}  // namespace gh

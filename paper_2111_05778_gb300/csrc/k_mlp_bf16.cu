@@ -29,9 +29,7 @@ namespace gh {
 
 namespace {
 
-constexpr int NTHREADS = 384;
 constexpr int EPI_T0 = 128;  // first epilogue thread (warp 4)
-constexpr int NEPI = 256;    // epilogue threads = rows per step
 constexpr int TM = 128;      // rows per tile
 constexpr int NSTAGE = 2;
 constexpr unsigned FULL = 0xFFFFFFFFu;
@@ -44,10 +42,11 @@ enum { MODE_HOP = 0, MODE_VERTS = 1, MODE_POINTS = 2 };
 
 template <int W>
 struct SmemB {
-    uint8_t a[2][W / 64][TM * 128];  // A operands: 2 tiles, K-blocks of 128 rows x 128 B (1024-aligned)
+    uint8_t a[2][W / 64][TM * 128];  // A operands: up to 2 tiles, K-blocks of 128 rows x 128 B (1024-aligned)
     uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
     float4 w0b[W];                   // layer 0: W0 row and bias
-    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full, a_full, drain;
+    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full, a_full, drain, item_ready;
+    const uint16_t *cur_wbf;  // weights of the item being processed
     uint32_t tmem_base;
     int ctl;
 };
@@ -161,16 +160,17 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-// OR-reduction over the 256 epilogue threads (named barrier 1).
+// OR-reduction over the NT epilogue threads (named barrier 1).
+template <int NT>
 __device__ __forceinline__ bool epi_any(bool v) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 256, p;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(NT)
         : "memory");
     return out != 0;
 }
@@ -181,22 +181,32 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, floa
 }
 
 // ---------------------------------------------------------------------------
-template <int W, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_mlp_bf16(MlpDev m, GridP g, Scratch s, const float *__restrict__ pts, long long npts, float *__restrict__ outv) {
+// TILES 128-row tiles per CTA (M = 128 * TILES rows per weight K-block).
+// A batch of items is walked in order: every CTA takes rows (rays or points)
+// from the shared per-item queues of item `cur`; when the item has no work
+// left for it, the CTA moves to the next item (reloading layer 0; the producer
+// reads the item's weights at the start of every step).
+template <int W, int MODE, int TILES>
+__global__ void __launch_bounds__(128 + 128 * TILES, 1)
+    k_mlp_bf16(const Item *__restrict__ items, int n_items, const float *__restrict__ pts, long long npts,
+               float *__restrict__ outv) {
     extern __shared__ uint8_t smem_raw[];
+    constexpr int NEPI = 128 * TILES;
     constexpr int KB = W / 64;
     constexpr uint32_t STAGE_BYTES = W * 128;
-    constexpr uint32_t TMEM_COLS = 2 * W;
+    constexpr uint32_t TMEM_COLS = TILES * W < 32 ? 32 : TILES * W;
     constexpr uint32_t IDESC = idesc_bf16(TM, W);
     SmemB<W> &sm = *reinterpret_cast<SmemB<W> *>(smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (MODE == MODE_VERTS && (s.ctr->flags & STOP_FLAGS)) return;  // uniform: nothing to evaluate
     volatile int *ctl = &sm.ctl;
+    Counters *ctr0 = items[0].s.ctr;  // error flags of a timeout go to the first item
+    const int n_mid = items[0].m.n_mid;
 
     // ---- set-up ----------------------------------------------------------
-    if (tid < W)
-        sm.w0b[tid] = make_float4(m.w0[3 * tid], m.w0[3 * tid + 1], m.w0[3 * tid + 2], m.b0[tid]);
+    if (tid < W) {
+        const MlpDev &m0 = items[0].m;
+        sm.w0b[tid] = make_float4(m0.w0[3 * tid], m0.w0[3 * tid + 1], m0.w0[3 * tid + 2], m0.b0[tid]);
+    }
     if (tid == 0) {
         for (int i = 0; i < NSTAGE; ++i) {
             mbar_init(&sm.full[i], 1);
@@ -205,7 +215,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(&sm.acc_full, 1);
         mbar_init(&sm.a_full, NEPI);
         mbar_init(&sm.drain, 1);
+        mbar_init(&sm.item_ready, 1);
         sm.ctl = 0;
+        sm.cur_wbf = items[0].m.wbf;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -220,36 +232,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t tmem = sm.tmem_base;
 
     if (warp == 0) {
-        // ---- TMA producer ----------------------------------------------------
+        // ---- TMA producer: the weights of the current item, step after step --
         if (lane == 0) {
-            const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(m.wbf);
-            const int nblk = m.n_mid * KB;
+            const int nblk = n_mid * KB;
             long long issued = 0;
-            for (int blk = 0;; blk = (blk + 1 == nblk) ? 0 : blk + 1) {
-                const int st = (int)(issued % NSTAGE);
-                const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
-                if (!wait_bar(&sm.empty[st], par, ctl, CTL_STOP | CTL_ABORT, s.ctr)) break;
-                mbar_expect_tx(&sm.full[st], STAGE_BYTES);
-                bulk_g2s(sm.w[st], wsrc + (size_t)blk * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
-                ++issued;
+            uint32_t pi = 0;
+            bool go = true;
+            while (go) {
+                if (!wait_bar(&sm.item_ready, pi, ctl, CTL_STOP | CTL_ABORT, ctr0)) break;
+                pi ^= 1u;
+                const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf);
+                for (int blk = 0; blk < nblk; ++blk) {
+                    const int st = (int)(issued % NSTAGE);
+                    const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
+                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_STOP | CTL_ABORT, ctr0)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_expect_tx(&sm.full[st], STAGE_BYTES);
+                    bulk_g2s(sm.w[st], wsrc + (size_t)blk * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
+                    ++issued;
+                }
             }
             // the copies still in flight land before the CTA may exit
             for (long long i = issued - NSTAGE; i < issued; ++i) {
                 if (i < 0) continue;
-                wait_bar(&sm.full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), ctl, 0, s.ctr);
+                wait_bar(&sm.full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), ctl, 0, ctr0);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---- MMA issuer --------------------------------------------------------
         if (lane == 0) {
-            const uint32_t a0 = su32(&sm.a[0][0][0]), a1 = su32(&sm.a[1][0][0]);
+            const uint32_t a0 = su32(&sm.a[0][0][0]), a1 = su32(&sm.a[TILES - 1][0][0]);
             long long consumed = 0;
             uint32_t pa = 0;
             bool go = true;
             while (go) {
-                for (int l = 0; l < m.n_mid && go; ++l) {
-                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, s.ctr) || (*ctl & CTL_STOP)) {
+                for (int l = 0; l < n_mid && go; ++l) {
+                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, ctr0) || (*ctl & CTL_STOP)) {
                         go = false;
                         break;
                     }
@@ -257,7 +278,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     tc_fence_after();
                     for (int kb = 0; kb < KB; ++kb) {
                         const int st = (int)(consumed % NSTAGE);
-                        if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, s.ctr)) {
+                        if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0)) {
                             go = false;
                             break;
                         }
@@ -267,7 +288,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         for (int k = 0; k < 4; ++k) {
                             const unsigned long long bd = sdesc(wb + k * 32);
                             umma(tmem, sdesc(a0 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
-                            umma(tmem + W, sdesc(a1 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
+                            if (TILES == 2)
+                                umma(tmem + W, sdesc(a1 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
                         }
                         umma_commit(&sm.empty[st]);
                         ++consumed;
@@ -277,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             // every MMA issued above has completed before TMEM is released
             umma_commit(&sm.drain);
-            wait_bar(&sm.drain, 0, ctl, 0, s.ctr);
+            wait_bar(&sm.drain, 0, ctl, 0, ctr0);
         }
         __syncwarp();
     } else if (warp >= 4) {
@@ -287,8 +309,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t arow = su32(&sm.a[t][0][0]) + (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
         const int sw = row & 7;
         const unsigned lt = (1u << lane) - 1u;
-        const int N = g.N;
-        const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+        int cur = 0;
+        const Item *it = &items[0];
         uint32_t col = NONE, rank = 0;
         int k = 0;
         bool done = false;
@@ -296,16 +318,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         unsigned long long evals = 0, idx = 0;
         uint32_t pacc = 0;
         for (;;) {
-            // 1. the work of this row
+            // 1. the work of this row, from item cur
+            const GridP &g = it->g;
+            const int N = g.N;
             bool live = false;
             float px = 0.f, py = 0.f, pz = 0.f;
             if (MODE == MODE_HOP) {
+                const uint32_t ncols = (uint32_t)N * (uint32_t)N;
                 const bool need = col == NONE && !done;
                 const unsigned needm = __ballot_sync(FULL, need);
                 if (needm) {
                     const int leader = __ffs(needm) - 1;
                     unsigned long long base = 0;
-                    if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
+                    if (lane == leader) base = atomicAdd(&it->s.ctr->next_col, (unsigned long long)__popc(needm));
                     base = __shfl_sync(FULL, base, leader);
                     if (need) {
                         const unsigned long long c = base + __popc(needm & lt);
@@ -328,20 +353,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     pz = fmaf((float)k + 0.5f, g.h, g.lo[2]);
                 }
             } else {
+                unsigned long long total = (unsigned long long)npts;
+                if (MODE == MODE_VERTS)
+                    total = (it->s.ctr->flags & STOP_FLAGS) ? 0ull : it->s.ctr->verts;
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&s.ctr->next_tile, 32ull);
+                if (lane == 0) base = done ? total : atomicAdd(&it->s.ctr->next_tile, 32ull);
                 base = __shfl_sync(FULL, base, 0);
                 idx = base + lane;
-                const unsigned long long total = MODE == MODE_VERTS ? s.ctr->verts : (unsigned long long)npts;
                 live = idx < total;
+                if (base >= total) done = true;
                 if (live) {
                     if (MODE == MODE_POINTS) {
                         px = pts[3 * idx];
                         py = pts[3 * idx + 1];
                         pz = pts[3 * idx + 2];
                     } else {
-                        const unsigned long long key = s.vkey[idx];
-                        const int N1 = g.N + 1;
+                        const unsigned long long key = it->s.vkey[idx];
+                        const int N1 = N + 1;
                         const uint32_t line = (uint32_t)(key & 0xFFFFFFFFull), c = (uint32_t)(key >> 32);
                         const uint32_t a = line / (uint32_t)N1, b = line - a * (uint32_t)N1;
                         px = fmaf((float)a, g.h, g.lo[0]);
@@ -351,16 +379,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             __syncwarp();
-            const bool any = epi_any(live);
-            if (!any || (*ctl & CTL_ABORT)) {
-                if (et == 0) {
-                    *ctl |= CTL_STOP;
-                    __threadfence_block();
-                }
-                epi_any(false);  // the stop bit is written before anyone arrives
+            const bool any = epi_any<NEPI>(live);
+            // the abort decision goes through the barrier so that it is uniform
+            if (epi_any<NEPI>((*ctl & CTL_ABORT) != 0)) {
                 mbar_arrive(&sm.a_full);
                 break;
             }
+            if (!any) {
+                // item cur has no work left for this CTA: next item, or stop
+                if (MODE == MODE_HOP) {
+                    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+                    if (lane == 0 && evals) atomicAdd(&it->s.ctr->hop_evals, evals);
+                    evals = 0;
+                }
+                ++cur;
+                if (cur >= n_items) {
+                    if (et == 0) {
+                        *ctl |= CTL_STOP;
+                        __threadfence_block();
+                    }
+                    epi_any<NEPI>(false);  // the stop bit is written before anyone arrives
+                    mbar_arrive(&sm.a_full);
+                    break;
+                }
+                it = &items[cur];
+                col = NONE;
+                done = false;
+                for (int o = et; o < W; o += NEPI) {
+                    const MlpDev &mm = it->m;
+                    sm.w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+                }
+                epi_any<NEPI>(false);  // layer-0 weights of the new item in place
+                continue;
+            }
+            if (et == 0) {
+                sm.cur_wbf = it->m.wbf;
+                mbar_arrive(&sm.item_ready);
+            }
+            const MlpDev &m = it->m;
             // 2. layer 0 (FP32) -> A operand
 #pragma unroll 1
             for (int o = 0; o < W; o += 8) {
@@ -379,13 +435,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive(&sm.a_full);
             // 3. hidden layers
             float gsum = 0.f;
-            for (int l = 0; l < m.n_mid; ++l) {
-                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, s.ctr);
+            for (int l = 0; l < n_mid; ++l) {
+                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, ctr0);
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
                 const float *bl = m.bm + (size_t)l * W;
-                if (l + 1 < m.n_mid) {
+                if (l + 1 < n_mid) {
 #pragma unroll 1
                     for (int j = 0; j < W / 32; ++j) {
                         float v[32];
@@ -428,10 +484,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // 4. f, then the hop step or the store
             const float f = outer_f(m, px, py, pz, gsum + m.bout);
             if (MODE == MODE_HOP) {
+                const Scratch &s = it->s;
                 bool mark = false;
                 int step = 1;
                 if (live) {
-                    ++evals;
                     float d = fabsf(f) - g.eps;
                     if (!isfinite(f)) {
                         atomicOr(&s.ctr->flags, FLAG_NONFINITE);
@@ -470,19 +526,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         col = NONE;
                     }
                 }
+                if (live) ++evals;
             } else if (live) {
                 if (MODE == MODE_VERTS) {
-                    if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
-                    s.vval[idx] = f;
+                    if (!isfinite(f)) atomicOr(&it->s.ctr->flags, FLAG_NONFINITE);
+                    it->s.vval[idx] = f;
                 } else {
                     outv[idx] = f;
                 }
             }
         }
-        if (MODE == MODE_HOP) {
-            for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
-            if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
-        }
+        (void)evals;
     }
     // ---- tear-down ---------------------------------------------------------
     tc_fence_before();
@@ -492,17 +546,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-template <int W, int MODE>
-void launch_bf16(const MlpDev &m, const GridP &g, Scratch &s, const float *p, long long n, float *out, int nsm,
-                 cudaStream_t st) {
+template <int W, int MODE, int TILES>
+void launch_bf16(const Item *items, int n_items, const float *p, long long n, float *out, int nsm, cudaStream_t st) {
     const size_t smem = sizeof(SmemB<W>) + 1024;
-    cudaFuncSetAttribute(k_mlp_bf16<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_mlp_bf16<W, MODE, TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int grid = nsm;
     if (MODE == MODE_POINTS) {
-        const long long tiles = (n + NEPI - 1) / NEPI;
+        const long long tiles = (n + 128 * TILES - 1) / (128 * TILES);
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
     }
-    k_mlp_bf16<W, MODE><<<grid, NTHREADS, smem, st>>>(m, g, s, p, n, out);
+    k_mlp_bf16<W, MODE, TILES><<<grid, 128 + 128 * TILES, smem, st>>>(items, n_items, p, n, out);
 }
 
 }  // namespace
@@ -516,23 +569,33 @@ void launch_bf16(const MlpDev &m, const GridP &g, Scratch &s, const float *p, lo
 
 bool bf16_supported(int width) { return width == 64 || width == 128 || width == 256; }
 
-void launch_hop_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
-    GH_BF16_W(m.width, launch_bf16<WW, MODE_HOP>(m, g, s, nullptr, 0, nullptr, nsm, st))
+#define GH_BF16_T(T, ...)                                \
+    if ((T) == 1) { constexpr int TT = 1; __VA_ARGS__; } \
+    else { constexpr int TT = 2; __VA_ARGS__; }
+
+void launch_hop_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st) {
+    GH_BF16_W(width, GH_BF16_T(tiles, (launch_bf16<WW, MODE_HOP, TT>(items, n_items, nullptr, 0, nullptr, nsm, st))))
 }
 
-void launch_eval_vertices_mlp_bf16(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
-    GH_BF16_W(m.width, launch_bf16<WW, MODE_VERTS>(m, g, s, nullptr, 0, nullptr, nsm, st))
+void launch_eval_vertices_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st) {
+    GH_BF16_W(width,
+              GH_BF16_T(tiles, (launch_bf16<WW, MODE_VERTS, TT>(items, n_items, nullptr, 0, nullptr, nsm, st))))
 }
 
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st) {
+    // one item whose counters live in a small private buffer
     static thread_local Counters *ctr = nullptr;
+    static thread_local Item *ditem = nullptr;
     if (!ctr) cudaMalloc(&ctr, sizeof(Counters));
+    if (!ditem) cudaMalloc(&ditem, sizeof(Item));
+    Item h{};
+    h.m = m;
+    h.s.ctr = ctr;
+    h.kind = 1;
     cudaMemsetAsync(ctr, 0, sizeof(Counters), st);
-    Scratch s{};
-    s.ctr = ctr;
-    GridP g{};
-    GH_BF16_W(m.width, launch_bf16<WW, MODE_POINTS>(m, g, s, p, n, out, nsm, st))
+    cudaMemcpyAsync(ditem, &h, sizeof(Item), cudaMemcpyHostToDevice, st);
+    GH_BF16_W(m.width, (launch_bf16<WW, MODE_POINTS, 2>(ditem, 1, p, n, out, nsm, st)))
 }
 
 }  // namespace gh

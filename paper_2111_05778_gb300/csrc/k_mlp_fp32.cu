@@ -147,20 +147,27 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float4 p, float g) {
     return (fmaf(m.alpha, g, r - m.r0) / m.beta) * m.inv_lam;
 }
 
+// Persistent hopper over a batch of items: the CTA's 128 rows take columns
+// from item cur's queue; when the item has no column left for this CTA and
+// all rows are done, the CTA moves to the next item.
 template <int W>
-__global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(MlpDev m, GridP g, Scratch s) {
+__global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int N = g.N;
-    const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+    int cur = 0;
     uint32_t col = NONE, rank = 0;
     int k = 0;
     bool done = false;
     float x = 0.f, y = 0.f;
     unsigned long long evals = 0;
-    for (;;) {
+    while (cur < n_items) {
+        const Item &it = items[cur];
+        const GridP &g = it.g;
+        const Scratch &s = it.s;
+        const int N = g.N;
+        const uint32_t ncols = (uint32_t)N * (uint32_t)N;
         bool live = false;
         if (tid < TM) {
             const bool need = col == NONE && !done;
@@ -187,13 +194,24 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(MlpDev m, GridP g, Scrat
             live = col != NONE;
             sm.p[tid] = live ? make_float4(x, y, fmaf((float)k + 0.5f, g.h, g.lo[2]), 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (!__syncthreads_or(live)) break;
-        mlp_tile<W>(m, sm);
+        if (!__syncthreads_or(live)) {
+            // item cur is finished for this CTA
+            if (tid < TM) {
+                for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+                if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+            }
+            evals = 0;
+            col = NONE;
+            done = false;
+            ++cur;
+            continue;
+        }
+        mlp_tile<W>(it.m, sm);
         if (tid < TM) {
             bool mark = false;
             int step = 1;
             if (live) {
-                const float f = outer_f(m, sm.p[tid], sm.g[tid]);
+                const float f = outer_f(it.m, sm.p[tid], sm.g[tid]);
                 ++evals;
                 float d = fabsf(f) - g.eps;
                 if (!isfinite(f)) {
@@ -236,34 +254,36 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(MlpDev m, GridP g, Scrat
         }
         // sm.p / sm.g are rewritten only after the barrier at the top of the next pass
     }
-    if (tid < TM) {
-        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
-        if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
-    }
 }
 
-// Point lists: MODE 0 = lattice vertices (vkey) of all unique vertices,
-// MODE 1 = vertices listed in s.rlist (refinement), MODE 2 = explicit points.
+// Point lists over a batch of items: MODE 0 = the unique lattice vertices of
+// each item, MODE 1 = each item's refinement list, MODE 2 = explicit points
+// (one item).
 template <int W, int MODE>
-__global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(MlpDev m, GridP g, Scratch s, const float *pts, long long npts,
-                                                         float *outv) {
+__global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__ items, int n_items,
+                                                         const float *pts, long long npts, float *outv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     __shared__ unsigned long long tile_s;
     __shared__ unsigned long long total_s;
     const int tid = threadIdx.x;
-    if (MODE != 2) {
-        if (s.ctr->flags & STOP_FLAGS) return;
-    }
-    unsigned long long* counter = MODE == 1 ? &s.ctr->next_tile2 : &s.ctr->next_tile;
-    for (;;) {
+    for (int cur = 0; cur < n_items;) {
+        const Item &it = items[cur];
+        const Scratch &s = it.s;
+        const GridP &g = it.g;
+        unsigned long long *counter = MODE == 1 ? &s.ctr->next_tile2 : &s.ctr->next_tile;
         if (tid == 0) {
-            tile_s = atomicAdd(counter, 1ull);
-            total_s = MODE == 0 ? s.ctr->verts : (MODE == 1 ? s.ctr->refine : (unsigned long long)npts);
+            const bool stopped = MODE != 2 && (s.ctr->flags & STOP_FLAGS);
+            total_s = stopped ? 0ull : (MODE == 0 ? s.ctr->verts : (MODE == 1 ? s.ctr->refine : (unsigned long long)npts));
+            tile_s = total_s ? atomicAdd(counter, 1ull) : 0ull;
         }
         __syncthreads();
         const unsigned long long t = tile_s, total = total_s;
-        if (t * TM >= total) break;
+        __syncthreads();
+        if (t * TM >= total) {
+            ++cur;
+            continue;
+        }
         if (tid < TM) {
             const unsigned long long r = t * TM + tid;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -282,11 +302,11 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(MlpDev m, GridP g, Scrat
             sm.p[tid] = p;
         }
         __syncthreads();
-        mlp_tile<W>(m, sm);
+        mlp_tile<W>(it.m, sm);
         if (tid < TM) {
             const unsigned long long r = t * TM + tid;
             if (r < total) {
-                const float f = outer_f(m, sm.p[tid], sm.g[tid]);
+                const float f = outer_f(it.m, sm.p[tid], sm.g[tid]);
                 if (MODE != 2 && !isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
                 if (MODE == 0) s.vval[r] = f;
                 else if (MODE == 1) s.vval[s.rlist[r]] = f;
@@ -314,43 +334,47 @@ int occupancy_grid(K kernel, size_t smem, int nsm) {
     default: { constexpr int WW = 256; __VA_ARGS__; } break;             \
     }
 
-void launch_hop_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
-    GH_DISPATCH_W(m.width, {
+void launch_hop_mlp_fp32(const Item *items, int n_items, int width, int nsm, cudaStream_t st) {
+    GH_DISPATCH_W(width, {
         const size_t smem = sizeof(Smem<WW>);
         const int grid = occupancy_grid(k_hop_mlp_fp32<WW>, smem, nsm);
-        k_hop_mlp_fp32<WW><<<grid, NT, smem, st>>>(m, g, s);
+        k_hop_mlp_fp32<WW><<<grid, NT, smem, st>>>(items, n_items);
     })
 }
 
-void launch_eval_vertices_mlp_fp32(const MlpDev &m, const GridP &g, Scratch &s, int nsm, bool refine_list,
+void launch_eval_vertices_mlp_fp32(const Item *items, int n_items, int width, int nsm, bool refine_list,
                                    cudaStream_t st) {
-    GH_DISPATCH_W(m.width, {
+    GH_DISPATCH_W(width, {
         const size_t smem = sizeof(Smem<WW>);
         if (refine_list) {
             const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 1>, smem, nsm);
-            k_pts_mlp_fp32<WW, 1><<<grid, NT, smem, st>>>(m, g, s, nullptr, 0, nullptr);
+            k_pts_mlp_fp32<WW, 1><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr);
         } else {
             const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 0>, smem, nsm);
-            k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(m, g, s, nullptr, 0, nullptr);
+            k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr);
         }
     })
 }
 
 void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st) {
-    // needs a counter: use a tiny private scratch on the stream
+    // one item whose counters live in a small private buffer
     static thread_local Counters *ctr = nullptr;
+    static thread_local Item *ditem = nullptr;
     if (!ctr) cudaMalloc(&ctr, sizeof(Counters));
+    if (!ditem) cudaMalloc(&ditem, sizeof(Item));
+    Item h{};
+    h.m = m;
+    h.s.ctr = ctr;
+    h.kind = 1;
     cudaMemsetAsync(ctr, 0, sizeof(Counters), st);
-    Scratch s{};
-    s.ctr = ctr;
-    GridP g{};
+    cudaMemcpyAsync(ditem, &h, sizeof(Item), cudaMemcpyHostToDevice, st);
     GH_DISPATCH_W(m.width, {
         const size_t smem = sizeof(Smem<WW>);
         int grid = occupancy_grid(k_pts_mlp_fp32<WW, 2>, smem, nsm);
         const long long tiles = (n + TM - 1) / TM;
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
-        k_pts_mlp_fp32<WW, 2><<<grid, NT, smem, st>>>(m, g, s, p, n, out);
+        k_pts_mlp_fp32<WW, 2><<<grid, NT, smem, st>>>(ditem, 1, p, n, out);
     })
 }
 

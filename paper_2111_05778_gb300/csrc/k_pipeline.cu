@@ -97,99 +97,110 @@ __global__ void k_init(Counters *c) {
 void launch_init(Scratch &s, cudaStream_t st) { k_init<<<1, 32, 0, st>>>(s.ctr); }
 
 // ---------------------------------------------------------------------------
-// 1. Persistent hopper for analytic SDBs.
+// 1. Persistent hopper for analytic SDBs over a batch of items.  Lanes take
+//    columns of item cur; a warp leaves the item when its lanes are done and
+//    the item's queue is empty; the CTA then moves on to the next item
+//    together (its primitives are staged in shared memory).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_hop_csg(const Prim *__restrict__ gprims, int nprim, GridP g, Scratch s) {
+__global__ void __launch_bounds__(512) k_hop_csg(const Item *__restrict__ items, int n_items) {
     extern __shared__ float4 sprim[];
-    load_prims(sprim, gprims, nprim);
-    const int N = g.N;
-    const uint32_t ncols = (uint32_t)N * (uint32_t)N;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t col = NONE, rank = 0;
-    int k = 0;
-    bool done = false;
-    float x = 0.f, y = 0.f;
-    unsigned long long evals = 0;
-    for (;;) {
-        const bool need = col == NONE && !done;
-        const unsigned needm = __ballot_sync(FULL, need);
-        if (needm) {
-            const int leader = __ffs(needm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
-            base = __shfl_sync(FULL, base, leader);
-            if (need) {
-                const unsigned long long c = base + __popc(needm & lt);
-                if (c < ncols) {
-                    col = (uint32_t)c;
-                    k = 0;
-                    rank = 0;
-                    const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
-                    x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
-                    y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+    for (int cur = 0; cur < n_items; ++cur) {
+        const Item &it = items[cur];
+        load_prims(sprim, it.prims, it.nprim);  // ends with __syncthreads
+        const int nprim = it.nprim;
+        const GridP g = it.g;
+        const Scratch &s = it.s;
+        const int N = g.N;
+        const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+        uint32_t col = NONE, rank = 0;
+        int k = 0;
+        bool done = false;
+        float x = 0.f, y = 0.f;
+        unsigned long long evals = 0;
+        for (;;) {
+            const bool need = col == NONE && !done;
+            const unsigned needm = __ballot_sync(FULL, need);
+            if (needm) {
+                const int leader = __ffs(needm) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&s.ctr->next_col, (unsigned long long)__popc(needm));
+                base = __shfl_sync(FULL, base, leader);
+                if (need) {
+                    const unsigned long long c = base + __popc(needm & lt);
+                    if (c < ncols) {
+                        col = (uint32_t)c;
+                        k = 0;
+                        rank = 0;
+                        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                        x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                        y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                    } else {
+                        done = true;
+                    }
+                }
+            }
+            const bool live = col != NONE;
+            if (!__any_sync(FULL, live)) break;
+            bool mark = false;
+            int step = 1;
+            if (live) {
+                const float z = fmaf((float)k + 0.5f, g.h, g.lo[2]);
+                const float f = csg_eval(sprim, nprim, x, y, z);
+                ++evals;
+                float d = fabsf(f) - g.eps;
+                if (!isfinite(f)) {
+                    atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                    d = 0.f;
+                }
+                if (d <= g.tau) {
+                    mark = true;
                 } else {
-                    done = true;
+                    const float stp = floorf(d * g.inv_h);
+                    step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
+                }
+            }
+            const unsigned mm = __ballot_sync(FULL, mark);
+            if (mm) {
+                const int leader = __ffs(mm) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
+                base = __shfl_sync(FULL, base, leader);
+                if (mark) {
+                    const unsigned long long idx = base + __popc(mm & lt);
+                    if (idx < (unsigned long long)s.cap_marks)
+                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
+                    else
+                        atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
+                }
+            }
+            if (live) {
+                if (mark) {
+                    ++rank;
+                    ++k;
+                } else {
+                    k += step;
+                }
+                if (k >= N) {
+                    s.colcount[col] = rank;
+                    col = NONE;
                 }
             }
         }
-        const bool live = col != NONE;
-        if (!__any_sync(FULL, live)) break;
-        bool mark = false;
-        int step = 1;
-        if (live) {
-            const float z = fmaf((float)k + 0.5f, g.h, g.lo[2]);
-            const float f = csg_eval(sprim, nprim, x, y, z);
-            ++evals;
-            float d = fabsf(f) - g.eps;
-            if (!isfinite(f)) {
-                atomicOr(&s.ctr->flags, FLAG_NONFINITE);
-                d = 0.f;
-            }
-            if (d <= g.tau) {
-                mark = true;
-            } else {
-                const float stp = floorf(d * g.inv_h);
-                step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
-            }
-        }
-        const unsigned mm = __ballot_sync(FULL, mark);
-        if (mm) {
-            const int leader = __ffs(mm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
-            base = __shfl_sync(FULL, base, leader);
-            if (mark) {
-                const unsigned long long idx = base + __popc(mm & lt);
-                if (idx < (unsigned long long)s.cap_marks)
-                    s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
-                else
-                    atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
-            }
-        }
-        if (live) {
-            if (mark) {
-                ++rank;
-                ++k;
-            } else {
-                k += step;
-            }
-            if (k >= N) {
-                s.colcount[col] = rank;
-                col = NONE;
-            }
-        }
+        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+        if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+        __syncthreads();  // the primitives are restaged only after every warp is done
     }
-    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
-    if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
 }
 
-void launch_hop_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm, cudaStream_t st) {
-    const size_t smem = (size_t)nprim * sizeof(Prim);
+void launch_hop_csg(const Item *items, int n_items, int max_prims, int nsm, int block, cudaStream_t st) {
+    const size_t smem = (size_t)max_prims * sizeof(Prim);
+    if (block != 128 && block != 512) block = 256;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_csg, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_csg, block, smem);
     if (per_sm < 1) per_sm = 1;
-    k_hop_csg<<<nsm * per_sm, 256, smem, st>>>(prims, nprim, g, s);
+    k_hop_csg<<<nsm * per_sm, block, smem, st>>>(items, n_items);
 }
 
 // ---------------------------------------------------------------------------

@@ -42,7 +42,7 @@ class SdbDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tau_mode", ctypes.c_int32), ("eps", ctypes.c_float),
-                ("sync", ctypes.c_int32)]
+                ("sync", ctypes.c_int32), ("ray_block", ctypes.c_int32), ("mlp_tiles", ctypes.c_int32)]
 
 
 STAT_FIELDS = ["status", "columns", "hop_evals", "marked_cells", "unique_vertices", "refined_vertices",
@@ -89,8 +89,9 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_float), P]),
                 "gh_polygonize": (ctypes.c_int, [ctypes.POINTER(Grid), P, ctypes.POINTER(Options),
                                                  ctypes.POINTER(MeshDesc), P]),
-                "gh_polygonize_batch": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.POINTER(Options), P, P,
-                                                       ctypes.POINTER(P)]),
+                "gh_polygonize_batch": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.POINTER(Options), P, P, P]),
+                "gh_batch_graph_launch": (ctypes.c_int, [P, P]),
+                "gh_batch_graph_free": (ctypes.c_int, [P]),
                 "gh_backward": (ctypes.c_int, [P, P, P, I64, P, P]),
                 "gh_eval": (ctypes.c_int, [P, P, I64, P, I32, P]),
                 "gh_mc_table": (ctypes.c_int, [P, P]),
@@ -114,7 +115,8 @@ def exported_symbols():
     """Names declared in include/gh.h that the library must export."""
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
-            "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc"]
+            "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc", "gh_batch_graph_launch",
+            "gh_batch_graph_free"]
 
 
 def check(rc):
@@ -276,21 +278,23 @@ class Buffers:
         return {n: int(v[i]) for i, n in enumerate(STAT_FIELDS)}
 
 
-def options(precision="fp32", tau_mode=GH_TAU_DIAGONAL, eps=None, sync=True) -> Options:
+def options(precision="fp32", tau_mode=GH_TAU_DIAGONAL, eps=None, sync=True, ray_block=0, mlp_tiles=0) -> Options:
     o = Options()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.tau_mode = int(tau_mode)
     o.eps = -1.0 if eps is None else float(eps)
     o.sync = 1 if sync else 0
+    o.ray_block = int(ray_block)
+    o.mlp_tiles = int(mlp_tiles)
     return o
 
 
 def polygonize_into(sdb: Sdb, N, bufs: Buffers, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_DIAGONAL,
-                    eps=None, sync=True, stream=None) -> int:
+                    eps=None, sync=True, stream=None, ray_block=0, mlp_tiles=0) -> int:
     """Runs gh_polygonize into preallocated buffers; returns the status code
     (GH_ERR_CAPACITY is returned, not raised)."""
     g = _grid(N, lo, hi)
-    o = options(precision, tau_mode, eps, sync)
+    o = options(precision, tau_mode, eps, sync, ray_block, mlp_tiles)
     rc = lib().gh_polygonize(ctypes.byref(g), sdb.handle, ctypes.byref(o), ctypes.byref(bufs.desc),
                              _stream_ptr(stream))
     if rc not in (GH_OK, GH_ERR_CAPACITY):
@@ -318,6 +322,78 @@ def polygonize(sdb: Sdb, N, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_D
     raise GhError(GH_ERR_CAPACITY, "output buffers kept overflowing")
 
 
+class Batch:
+    """A batch of polygonizations bound to caller-owned buffers (one Buffers
+    per item): run() executes gh_polygonize_batch; capture() builds a CUDA
+    graph of the same launches that replay() re-runs."""
+
+    def __init__(self, sdbs, Ns, caps, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0,
+                 mlp_tiles=0):
+        self.sdbs = list(sdbs)
+        self.Ns = [int(n) for n in Ns]
+        self.B = len(self.sdbs)
+        self.bufs = [Buffers(c, keys=keys) for c in caps]
+        self.grids = (Grid * self.B)(*[_grid(n, lo, hi) for n in self.Ns])
+        self.handles = (ctypes.c_void_p * self.B)(*[s_.handle for s_ in self.sdbs])
+        self.meshes = (MeshDesc * self.B)(*[b.desc for b in self.bufs])
+        self.opts = options(precision, GH_TAU_DIAGONAL, eps, True, ray_block, mlp_tiles)
+        self.graph = None
+
+    def run(self, sync=True, stream=None) -> int:
+        self.opts.sync = 1 if sync else 0
+        rc = lib().gh_polygonize_batch(self.B, self.grids, self.handles, ctypes.byref(self.opts), self.meshes,
+                                       _stream_ptr(stream), None)
+        if rc not in (GH_OK, GH_ERR_CAPACITY):
+            check(rc)
+        return rc
+
+    def capture(self, stream=None):
+        g = ctypes.c_void_p()
+        check(lib().gh_polygonize_batch(self.B, self.grids, self.handles, ctypes.byref(self.opts), self.meshes,
+                                        _stream_ptr(stream), ctypes.byref(g)))
+        self.graph = g
+        return g
+
+    def replay(self, stream=None):
+        check(lib().gh_batch_graph_launch(self.graph, _stream_ptr(stream)))
+
+    def close(self):
+        if self.graph is not None and _lib is not None:
+            _lib.gh_batch_graph_free(self.graph)
+            self.graph = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def counts(self):
+        import torch
+
+        return torch.stack([b.counts[0] for b in self.bufs]).cpu().numpy()
+
+    def mesh(self, b) -> "Mesh":
+        T = int(self.bufs[b].counts[0].item())
+        bb = self.bufs[b]
+        return Mesh(bb.tri_xyz[:T], bb.tri_keys[:T] if bb.tri_keys is not None else None, None, None,
+                    bb.stats_dict())
+
+
+def polygonize_batch(sdbs, Ns, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0, mlp_tiles=0):
+    """gh_polygonize_batch with per-item buffers sized automatically; returns
+    the Batch (its meshes via .mesh(b))."""
+    caps = [4 * n * n + 4096 for n in Ns]
+    for _ in range(3):
+        bt = Batch(sdbs, Ns, caps, lo, hi, precision, keys, eps, ray_block, mlp_tiles)
+        rc = bt.run(sync=True)
+        if rc == GH_OK:
+            return bt
+        need = bt.counts()
+        caps = [int(max(c, n) * 1.1) + 4096 for c, n in zip(caps, need)]
+    raise GhError(GH_ERR_CAPACITY, "batch buffers kept overflowing")
+
+
 NOALLOC_MAX_N = 256
 
 
@@ -342,6 +418,31 @@ def polygonize_csg_noalloc(prims_dev, n_prim, N, bufs: Buffers, lo=-1.0, hi=1.0,
     if rc not in (GH_OK, GH_ERR_CAPACITY):
         check(rc)
     return rc
+
+
+def backward(sdb: "MlpSdb", verts, dl_dv, stream=None):
+    """gh_backward: dL/dtheta (packed like the MLP parameters) of a loss on mesh
+    vertices, through the implicit rule dv/dtheta = -grad f (df/dtheta)/|grad f|^2."""
+    import torch
+
+    v = verts.detach().contiguous().to(torch.float32)
+    g = dl_dv.detach().contiguous().to(torch.float32)
+    out = torch.empty(sdb.params.size, dtype=torch.float32, device=v.device)
+    check(lib().gh_backward(sdb.handle, v.data_ptr(), g.data_ptr(), v.shape[0], out.data_ptr(),
+                            _stream_ptr(stream)))
+    return out
+
+
+def unique_vertices(mesh: "Mesh"):
+    """Indexed mesh from the triangle soup: vertices deduplicated by edge key
+    (equal keys carry bit-identical positions), faces [T,3] into them."""
+    import torch
+
+    keys = mesh.tri_keys.reshape(-1)
+    uk, inv = torch.unique(keys, return_inverse=True)
+    verts = torch.empty((uk.numel(), 3), dtype=mesh.tri_xyz.dtype, device=keys.device)
+    verts[inv] = mesh.tri_xyz.reshape(-1, 3)
+    return verts, inv.reshape(-1, 3), uk
 
 
 def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):

@@ -1,0 +1,85 @@
+"""GPU implicit-surface adjoint (gh_backward behind torch.autograd) for the
+C4 workload: the width-256 network of seed 1 at N = 256, FP32; loss = mean
+over the unique mesh vertices of (|v - c| - 0.55)^2 with a seeded target
+centre c.  Checked against the FP64 oracle's adjoint on the same vertices and
+against FP64 central finite differences (step 1e-4) of the implicit loss on
+32 random weights."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2111_05778_gb300 import autograd, gh, synth  # noqa: E402
+
+R_TARGET = 0.55
+
+
+def _target():
+    return np.random.default_rng(4).uniform(-0.05, 0.05, 3)
+
+
+def _setup(width=256, seed=1, N=256):
+    params = synth.mlp_params(seed, width)
+    p = torch.from_numpy(params).cuda().requires_grad_(True)
+    c = torch.tensor(_target(), dtype=torch.float32, device="cuda")
+    verts, faces = autograd.polygonize_mlp(p, width, synth.MLP_NMID, N)
+    loss = ((verts - c).norm(dim=1) - R_TARGET).pow(2).mean()
+    loss.backward()
+    return params, verts.detach().cpu().numpy().astype(np.float64), p.grad.cpu().numpy().astype(np.float64)
+
+
+def _rel_ok(g, ref, floor_frac=1e-2, tol=1e-3):
+    scale = np.maximum(np.abs(ref), floor_frac * np.abs(ref).max())
+    return np.abs(g - ref) <= tol * scale
+
+
+def test_adjoint_matches_oracle_and_finite_differences():
+    width, nmid = 256, synth.MLP_NMID
+    params, V, g = _setup(width)
+    assert V.shape[0] > 50000
+    c = _target()
+    r = np.linalg.norm(V - c, axis=1)
+    dldv = (2 * (r - R_TARGET) / r)[:, None] * (V - c) / V.shape[0]
+    p64 = params.astype(np.float64)
+    g_or = oracle.np_adjoint(p64, width, nmid, V, dldv)
+    ok = _rel_ok(g, g_or)
+    assert ok.mean() > 0.999, "adjoint vs oracle: %.5f within 1e-3" % ok.mean()
+    # FP64 finite differences of the implicit loss (its derivative at theta is the adjoint)
+    f0 = oracle.np_eval(p64, width, nmid, V)
+    gx = oracle.np_grad_x(p64, width, nmid, V)
+    n2 = (gx * gx).sum(1)
+
+    def implicit_loss(pp):
+        f1 = oracle.np_eval(pp, width, nmid, V)
+        v = V - ((f1 - f0) / n2)[:, None] * gx
+        return np.mean((np.linalg.norm(v - c, axis=1) - R_TARGET) ** 2)
+
+    rng = np.random.default_rng(12)
+    idx = rng.choice(params.size, 32, replace=False)
+    d = 1e-4
+    fd = np.empty(32)
+    for q, i in enumerate(idx):
+        hi = p64.copy()
+        lo = p64.copy()
+        hi[i] += d
+        lo[i] -= d
+        fd[q] = (implicit_loss(hi) - implicit_loss(lo)) / (2 * d)
+    assert _rel_ok(g[idx], fd).all(), np.c_[g[idx], fd]
+    assert _rel_ok(g_or[idx], fd).all()
+
+
+def test_adjoint_is_deterministic_and_chunked():
+    sdb = gh.MlpSdb(synth.mlp_params(2, 64), 64)
+    rng = np.random.default_rng(0)
+    V = torch.from_numpy(rng.uniform(-0.7, 0.7, (150001, 3)).astype(np.float32)).cuda()
+    G = torch.from_numpy(rng.normal(size=(150001, 3)).astype(np.float32)).cuda()
+    a = gh.backward(sdb, V, G)
+    b = gh.backward(sdb, V, G)
+    assert torch.equal(a, b)
+    ref = oracle.np_adjoint(sdb.params.astype(np.float64), 64, 5, V.cpu().numpy(), G.cpu().numpy())
+    assert _rel_ok(a.cpu().numpy().astype(np.float64), ref).mean() > 0.999
+    z = gh.backward(sdb, V[:0], G[:0])
+    assert (z == 0).all()

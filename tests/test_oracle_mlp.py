@@ -139,3 +139,18 @@ def test_adjoint_matches_implicit_fd_target():
         # relative error, floored at 1e-6 of the largest component (the FD
         # round-off is about 1e-19 / (2 d) in absolute terms)
         assert abs(g[i] - fd) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (i, g[i], fd)
+
+
+def test_numpy_helpers_match_the_c_oracle():
+    """The matmul-based FP64 helpers restate the C oracle's definitions; they
+    must agree with it (values, input gradient, adjoint)."""
+    w, nmid = 32, 3
+    params = synth.mlp_params(6, w, nmid).astype(np.float64)
+    s = oracle.mlp(w, nmid, params, lam=1.2)
+    rng = np.random.default_rng(4)
+    P = rng.uniform(-0.9, 0.9, (300, 3))
+    np.testing.assert_allclose(oracle.np_eval(params, w, nmid, P, lam=1.2), s.eval(P), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(oracle.np_grad_x(params, w, nmid, P, lam=1.2), s.grad_x(P), rtol=1e-12, atol=1e-14)
+    G = rng.normal(size=P.shape)
+    np.testing.assert_allclose(oracle.np_adjoint(params, w, nmid, P, G, lam=1.2), s.adjoint(P, G), rtol=1e-10,
+                               atol=1e-14)
