@@ -292,7 +292,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     const float *wout = mid + (size_t)h.n_mid * ((size_t)W * W + W);
     // FP32 hidden weights: transposed (in-major) with the outputs of a row
     // permuted so that thread group og reads 16 contiguous bytes per step:
-    // position q*64 + og*4 + e holds output og*(W/16) + q*4 + e.
+    // position q*64 + og*4 + e holds output og + 16*(4q + e).
     std::vector<float> wt((size_t)h.n_mid * W * W), bm((size_t)h.n_mid * W);
     const int TO = W / 16;
     for (int l = 0; l < h.n_mid; ++l) {
@@ -301,7 +301,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
             for (int q = 0; q < TO / 4; ++q)
                 for (int og = 0; og < 16; ++og)
                     for (int e = 0; e < 4; ++e) {
-                        const int o = og * TO + q * 4 + e;
+                        const int o = og + 16 * (4 * q + e);
                         wt[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)o * W + i];
                     }
         for (int o = 0; o < W; ++o) bm[(size_t)l * W + o] = bl[o];
@@ -899,11 +899,18 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
             cudaFree(d_items);
             return rc;
         }
-        // capture the same sequence into a graph bound to these buffers
+        // capture the same sequence into a graph bound to these buffers, on a
+        // private stream (the legacy default stream can not be captured)
         cudaGraph_t gr = nullptr;
-        GH_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        const int erc = batch_enqueue(P, B, sd.data(), o, outs, nsm, st);
-        const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+        cudaStream_t cs = nullptr;
+        GH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int erc = GH_OK;
+        if (ec == cudaSuccess) {
+            erc = batch_enqueue(P, B, sd.data(), o, outs, nsm, cs);
+            ec = cudaStreamEndCapture(cs, &gr);
+        }
+        cudaStreamDestroy(cs);
         if (erc || ec != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);
             cudaFree(d_items);

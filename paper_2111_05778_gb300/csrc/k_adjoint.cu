@@ -175,7 +175,7 @@ __global__ void k_adj_reduce(const float *__restrict__ part, int splits, long lo
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         float acc = 0.f;
         for (int z = 0; z < splits; ++z) acc += part[(size_t)z * n + i];
-        out[i] = accumulate ? out[i] + c * acc : c * acc;
+        out[i] = accumulate ? __fadd_rn(out[i], __fmul_rn(c, acc)) : __fmul_rn(c, acc);
     }
 }
 

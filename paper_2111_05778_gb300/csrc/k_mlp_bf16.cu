@@ -45,6 +45,8 @@ struct SmemB {
     uint8_t a[2][W / 64][TM * 128];  // A operands: up to 2 tiles, K-blocks of 128 rows x 128 B (1024-aligned)
     uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
     float4 w0b[W];                   // layer 0: W0 row and bias
+    float bmid[16 * W];              // hidden-layer biases (n_mid <= 16)
+    float wout[W];                   // output-layer weights
     unsigned long long full[NSTAGE], empty[NSTAGE], acc_full, a_full, drain, item_ready;
     const uint16_t *cur_wbf;  // weights of the item being processed
     uint32_t tmem_base;
@@ -135,6 +137,23 @@ __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this thread's lane; completes at the
+// next tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
@@ -203,9 +222,13 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     const int n_mid = items[0].m.n_mid;
 
     // ---- set-up ----------------------------------------------------------
-    if (tid < W) {
+    {
         const MlpDev &m0 = items[0].m;
-        sm.w0b[tid] = make_float4(m0.w0[3 * tid], m0.w0[3 * tid + 1], m0.w0[3 * tid + 2], m0.b0[tid]);
+        if (tid < W) {
+            sm.w0b[tid] = make_float4(m0.w0[3 * tid], m0.w0[3 * tid + 1], m0.w0[3 * tid + 2], m0.b0[tid]);
+            sm.wout[tid] = m0.wout[tid];
+        }
+        for (int i = tid; i < n_mid * W; i += blockDim.x) sm.bmid[i] = m0.bm[i];
     }
     if (tid == 0) {
         for (int i = 0; i < NSTAGE; ++i) {
@@ -405,9 +428,13 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 it = &items[cur];
                 col = NONE;
                 done = false;
-                for (int o = et; o < W; o += NEPI) {
+                {
                     const MlpDev &mm = it->m;
-                    sm.w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+                    for (int o = et; o < W; o += NEPI) {
+                        sm.w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+                        sm.wout[o] = mm.wout[o];
+                    }
+                    for (int i = et; i < n_mid * W; i += NEPI) sm.bmid[i] = mm.bm[i];
                 }
                 epi_any<NEPI>(false);  // layer-0 weights of the new item in place
                 continue;
@@ -440,43 +467,55 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
-                const float *bl = m.bm + (size_t)l * W;
+                const float *bl = sm.bmid + l * W;
+                uint32_t ra[32], rb[32];
+                tmem_ld32_async(taddr, ra);
+                tmem_wait_ld();
                 if (l + 1 < n_mid) {
-#pragma unroll 1
+#pragma unroll
                     for (int j = 0; j < W / 32; ++j) {
-                        float v[32];
-                        tmem_ld32(taddr + 32 * j, v);
+                        // the next chunk's load runs while this one is converted
+                        uint32_t(&cu)[32] = (j & 1) ? rb : ra;
+                        uint32_t(&nx)[32] = (j & 1) ? ra : rb;
+                        if (j + 1 < W / 32) tmem_ld32_async(taddr + 32 * (j + 1), nx);
                         const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
                         const int kb = j >> 1, c0 = (j & 1) * 4;
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const float4 b0 = __ldg(bp + 2 * c), b1 = __ldg(bp + 2 * c + 1);
-                            const uint32_t p0 = pack_relu_bf16(v[8 * c + 0] + b0.x, v[8 * c + 1] + b0.y);
-                            const uint32_t p1 = pack_relu_bf16(v[8 * c + 2] + b0.z, v[8 * c + 3] + b0.w);
-                            const uint32_t p2 = pack_relu_bf16(v[8 * c + 4] + b1.x, v[8 * c + 5] + b1.y);
-                            const uint32_t p3 = pack_relu_bf16(v[8 * c + 6] + b1.z, v[8 * c + 7] + b1.w);
+                            const float4 b0 = bp[2 * c], b1 = bp[2 * c + 1];
+                            const uint32_t p0 = pack_relu_bf16(__uint_as_float(cu[8 * c + 0]) + b0.x,
+                                                               __uint_as_float(cu[8 * c + 1]) + b0.y);
+                            const uint32_t p1 = pack_relu_bf16(__uint_as_float(cu[8 * c + 2]) + b0.z,
+                                                               __uint_as_float(cu[8 * c + 3]) + b0.w);
+                            const uint32_t p2 = pack_relu_bf16(__uint_as_float(cu[8 * c + 4]) + b1.x,
+                                                               __uint_as_float(cu[8 * c + 5]) + b1.y);
+                            const uint32_t p3 = pack_relu_bf16(__uint_as_float(cu[8 * c + 6]) + b1.z,
+                                                               __uint_as_float(cu[8 * c + 7]) + b1.w);
                             sts128(arow + kb * (TM * 128) + (((c0 + c) ^ sw) << 4), p0, p1, p2, p3);
                         }
+                        tmem_wait_ld();
                     }
                     tc_fence_before();
                     fence_async_smem();
                     mbar_arrive(&sm.a_full);
                 } else {
                     // output layer in FP32 from the accumulators
-#pragma unroll 1
+#pragma unroll
                     for (int j = 0; j < W / 32; ++j) {
-                        float v[32];
-                        tmem_ld32(taddr + 32 * j, v);
+                        uint32_t(&cu)[32] = (j & 1) ? rb : ra;
+                        uint32_t(&nx)[32] = (j & 1) ? ra : rb;
+                        if (j + 1 < W / 32) tmem_ld32_async(taddr + 32 * (j + 1), nx);
                         const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
-                        const float4 *wp = reinterpret_cast<const float4 *>(m.wout + 32 * j);
+                        const float4 *wp = reinterpret_cast<const float4 *>(sm.wout + 32 * j);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            const float4 b = __ldg(bp + c), w = __ldg(wp + c);
-                            gsum = fmaf(w.x, fmaxf(v[4 * c + 0] + b.x, 0.f), gsum);
-                            gsum = fmaf(w.y, fmaxf(v[4 * c + 1] + b.y, 0.f), gsum);
-                            gsum = fmaf(w.z, fmaxf(v[4 * c + 2] + b.z, 0.f), gsum);
-                            gsum = fmaf(w.w, fmaxf(v[4 * c + 3] + b.w, 0.f), gsum);
+                            const float4 b = bp[c], w = wp[c];
+                            gsum = fmaf(w.x, fmaxf(__uint_as_float(cu[4 * c + 0]) + b.x, 0.f), gsum);
+                            gsum = fmaf(w.y, fmaxf(__uint_as_float(cu[4 * c + 1]) + b.y, 0.f), gsum);
+                            gsum = fmaf(w.z, fmaxf(__uint_as_float(cu[4 * c + 2]) + b.z, 0.f), gsum);
+                            gsum = fmaf(w.w, fmaxf(__uint_as_float(cu[4 * c + 3]) + b.w, 0.f), gsum);
                         }
+                        tmem_wait_ld();
                     }
                     tc_fence_before();
                 }

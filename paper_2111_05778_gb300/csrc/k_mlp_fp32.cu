@@ -72,14 +72,19 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
             sm.act[o][r] = fmaxf(z, 0.f);
         }
     }
+    // thread (og, rg): rows rg*8 .. rg*8+7, outputs og + 16 j (j < TO); the
+    // weight chunk holds, at q*64 + og*4 + e, the weights of output og + 16(4q + e),
+    // so each thread reads 16 contiguous bytes and the activation write-back
+    // below stores consecutive rows from consecutive lanes.  Products run as
+    // packed FP32 pairs (fma.rn.f32x2: outputs 2p and 2p+1 of the thread).
     const int og = tid & 15, rg = tid >> 4;
     int ch = 0;
     for (int l = 0; l < m.n_mid; ++l) {
-        float acc[8][TO];
+        unsigned long long acc[8][TO / 2];
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
-            for (int o = 0; o < TO; ++o) acc[rr][o] = 0.f;
+            for (int p = 0; p < TO / 2; ++p) acc[rr][p] = 0ull;
         for (int c = 0; c < NCH; ++c, ++ch) {
             if (ch + 1 < nchunks) {
                 issue_chunk<W>(m, ch + 1, sm.wbuf[(ch + 1) & 1]);
@@ -95,15 +100,16 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
                 const float4 a0 = *reinterpret_cast<const float4 *>(&sm.act[i][rg * 8]);
                 const float4 a1 = *reinterpret_cast<const float4 *>(&sm.act[i][rg * 8 + 4]);
                 const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                unsigned long long a2[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) asm("mov.b64 %0, {%1, %1};" : "=l"(a2[rr]) : "f"(a[rr]));
 #pragma unroll
                 for (int q = 0; q < TO / 4; ++q) {
-                    const float4 w = *reinterpret_cast<const float4 *>(wb + kk * W + q * 64 + og * 4);
+                    const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(wb + kk * W + q * 64 + og * 4);
 #pragma unroll
                     for (int rr = 0; rr < 8; ++rr) {
-                        acc[rr][q * 4 + 0] = fmaf(a[rr], w.x, acc[rr][q * 4 + 0]);
-                        acc[rr][q * 4 + 1] = fmaf(a[rr], w.y, acc[rr][q * 4 + 1]);
-                        acc[rr][q * 4 + 2] = fmaf(a[rr], w.z, acc[rr][q * 4 + 2]);
-                        acc[rr][q * 4 + 3] = fmaf(a[rr], w.w, acc[rr][q * 4 + 3]);
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[rr][2 * q]) : "l"(a2[rr]), "l"(w.x));
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[rr][2 * q + 1]) : "l"(a2[rr]), "l"(w.y));
                     }
                 }
             }
@@ -112,23 +118,28 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
         // bias + ReLU, back into the activation buffer
         const float *bl = m.bm + (size_t)l * W;
 #pragma unroll
-        for (int q = 0; q < TO / 4; ++q)
+        for (int p = 0; p < TO / 2; ++p) {
+            float lo[8], hi[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int o = og * TO + q * 4 + e;
+            for (int rr = 0; rr < 8; ++rr) asm("mov.b64 {%0, %1}, %2;" : "=f"(lo[rr]), "=f"(hi[rr]) : "l"(acc[rr][p]));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float *v = h ? hi : lo;
+                const int o = og + 16 * (2 * p + h);
                 const float b = __ldg(bl + o);
                 float4 v0, v1;
-                v0.x = fmaxf(acc[0][q * 4 + e] + b, 0.f);
-                v0.y = fmaxf(acc[1][q * 4 + e] + b, 0.f);
-                v0.z = fmaxf(acc[2][q * 4 + e] + b, 0.f);
-                v0.w = fmaxf(acc[3][q * 4 + e] + b, 0.f);
-                v1.x = fmaxf(acc[4][q * 4 + e] + b, 0.f);
-                v1.y = fmaxf(acc[5][q * 4 + e] + b, 0.f);
-                v1.z = fmaxf(acc[6][q * 4 + e] + b, 0.f);
-                v1.w = fmaxf(acc[7][q * 4 + e] + b, 0.f);
+                v0.x = fmaxf(v[0] + b, 0.f);
+                v0.y = fmaxf(v[1] + b, 0.f);
+                v0.z = fmaxf(v[2] + b, 0.f);
+                v0.w = fmaxf(v[3] + b, 0.f);
+                v1.x = fmaxf(v[4] + b, 0.f);
+                v1.y = fmaxf(v[5] + b, 0.f);
+                v1.z = fmaxf(v[6] + b, 0.f);
+                v1.w = fmaxf(v[7] + b, 0.f);
                 *reinterpret_cast<float4 *>(&sm.act[o][rg * 8]) = v0;
                 *reinterpret_cast<float4 *>(&sm.act[o][rg * 8 + 4]) = v1;
             }
+        }
     }
     __syncthreads();
     {  // output layer W -> 1

@@ -539,11 +539,13 @@ void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStre
 }
 
 // ---------------------------------------------------------------------------
-// FP32 refinement of the BF16 path: every corner of a marked cell whose BF16
-// corner values are not all > eps or all < -eps (so whose FP32 signs could
-// differ or which may hold the surface) is re-evaluated in FP32.  Cells whose
-// values all clear eps keep their case (0 or 255) whatever the refined values
-// of shared corners, because |f_bf16 - f_fp32| <= eps / 2.
+// FP32 refinement of the BF16 path.  Marching Cubes on a cell needs the sign
+// of each corner and the value at both ends of each crossing edge.  With
+// |f_bf16 - f_fp32| <= eps / 2, a corner whose BF16 value clears +-eps has its
+// FP32 sign already, and an edge can cross in FP32 only if its BF16 end
+// values differ in sign or one of them lies within eps of 0.  So only the
+// endpoints of such edges are re-evaluated in FP32; every other corner keeps
+// its BF16 value, of which only the (certain) sign is ever used.
 // ---------------------------------------------------------------------------
 __global__ void k_refine_zero(Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
@@ -557,28 +559,35 @@ __global__ void k_refine_select(GridP g, Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
     const unsigned long long M = s.ctr->marks;
     const int N = g.N, N1 = N + 1;
+    // the 12 cube edges as corner pairs (corner b at (b&1, b>>1&1, b>>2&1))
+    const uint8_t ea[12] = {0, 2, 4, 6, 0, 1, 4, 5, 0, 1, 2, 3};
+    const uint8_t eb[12] = {1, 3, 5, 7, 2, 3, 6, 7, 4, 5, 6, 7};
     for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
          m += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long r = s.marks_csr[m];
         const uint32_t col = mark_col(r), k = mark_k(r);
         const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
-        uint32_t idx[4];
-        bool allpos = true, allneg = true;
+        uint32_t vi[8];
+        float fv[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
-            idx[q] = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], k);
-            const float a = s.vval[idx[q]], b = s.vval[idx[q] + 1];
-            allpos = allpos && a > g.eps && b > g.eps;
-            allneg = allneg && a < -g.eps && b < -g.eps;
+            const uint32_t idx = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], k);
+            vi[q] = idx;
+            vi[q + 4] = idx + 1;
+            fv[q] = s.vval[idx];
+            fv[q + 4] = s.vval[idx + 1];
         }
-        if (!allpos && !allneg) {
+        uint32_t need = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s.vflag[idx[q]] = 1;
-                s.vflag[idx[q] + 1] = 1;
-            }
+        for (int e = 0; e < 12; ++e) {
+            const float a = fv[ea[e]], b = fv[eb[e]];
+            if ((a < 0.f) != (b < 0.f) || fabsf(a) <= g.eps || fabsf(b) <= g.eps)
+                need |= (1u << ea[e]) | (1u << eb[e]);
         }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (need & (1u << c)) s.vflag[vi[c]] = 1;
     }
 }
 
