@@ -258,18 +258,20 @@ int gh_eval(const gh_sdb *sdb, const float *p, int64_t n, float *out, int32_t pr
 
 /* Profiling aid.  gh_set_profiling(1) makes every later gh_polygonize on the
  * calling thread record CUDA events on its stream around its phases (ray
- * hopping, vertex lists, vertex evaluation, FP32 refinement, Marching Cubes).
+ * hopping, vertex lists, vertex evaluation, selection of the vertices to
+ * refine, FP32 refinement, Marching Cubes).
  * gh_last_profile waits for those events and reports the phase durations of
  * the last call; `launches` (the number of kernels that call launched) is
  * reported whether or not profiling is on. */
 #define GH_PHASE_HOP 0
 #define GH_PHASE_LISTS 1
 #define GH_PHASE_VERTICES 2
-#define GH_PHASE_REFINE 3
-#define GH_PHASE_MC 4
+#define GH_PHASE_SELECT 3
+#define GH_PHASE_REFINE 4
+#define GH_PHASE_MC 5
 typedef struct {
     int64_t launches;
-    int32_t n_phases; /* 5 when timed, 0 when profiling was off */
+    int32_t n_phases; /* 6 when timed, 0 when profiling was off */
     int32_t reserved;
     double ms[8];
 } gh_profile;

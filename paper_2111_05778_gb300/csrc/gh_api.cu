@@ -503,7 +503,7 @@ static int check_mesh(const gh_mesh *m) {
 struct ProfState {
     bool enabled = false;
     bool recorded = false;
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[7] = {};
     long long launches = 0;
 };
 static thread_local ProfState g_prof;
@@ -520,13 +520,13 @@ extern "C" int gh_last_profile(gh_profile *out) {
     memset(out, 0, sizeof(*out));
     out->launches = g_prof.launches;
     if (!g_prof.recorded) return GH_OK;
-    GH_CUDA(cudaEventSynchronize(g_prof.ev[5]));
-    for (int p = 0; p < 5; ++p) {
+    GH_CUDA(cudaEventSynchronize(g_prof.ev[6]));
+    for (int p = 0; p < 6; ++p) {
         float ms = 0.f;
         GH_CUDA(cudaEventElapsedTime(&ms, g_prof.ev[p], g_prof.ev[p + 1]));
         out->ms[p] = ms;
     }
-    out->n_phases = 5;
+    out->n_phases = 6;
     return GH_OK;
 }
 
@@ -555,6 +555,7 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
         launch_eval_vertices_csg(s->d_prims, s->nprim, g, c, nsm, st);
         mark_phase(3, st);
         mark_phase(4, st);
+        mark_phase(5, st);
     } else if (o.precision == GH_FP32) {
         launch_hop_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, st);
         mark_phase(1, st);
@@ -563,6 +564,7 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
         launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, false, st);
         mark_phase(3, st);
         mark_phase(4, st);
+        mark_phase(5, st);
     } else {
         launch_hop_mlp_bf16(s->d_item, 1, s->mlp.width, nsm, tiles, st);
         mark_phase(1, st);
@@ -571,13 +573,14 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
         launch_eval_vertices_mlp_bf16(s->d_item, 1, s->mlp.width, nsm, tiles, st);
         mark_phase(3, st);
         launch_refine_select(g, c, st);
-        launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, true, st);
         mark_phase(4, st);
+        launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, true, st);
+        mark_phase(5, st);
         launches += LAUNCHES_REFINE;
     }
     launch_mc(g, c, out, nsm, st);
     launch_finalize(c, out, (long long)g.N * g.N, st);
-    mark_phase(5, st);
+    mark_phase(6, st);
     g_prof.recorded = g_prof.enabled;
     g_prof.launches = launches;
     GH_CUDA(cudaGetLastError());

@@ -64,7 +64,7 @@ class Profile(ctypes.Structure):
                 ("ms", ctypes.c_double * 8)]
 
 
-PHASES = ["hop", "lists", "vertices", "refine", "mc"]
+PHASES = ["hop", "lists", "vertices", "select", "refine", "mc"]
 
 
 def lib_path() -> str:
