@@ -242,13 +242,21 @@ int gh_batch_graph_free(void *graph);
 int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim, int32_t tau_mode,
                               gh_mesh *out, void *stream);
 
-/* Implicit-surface adjoint for a neural SDB: given mesh vertices v[V][3]
- * (device, float32) and the loss gradient dL/dv[V][3] (device), accumulates
+/* Implicit-surface adjoint: given mesh vertices v[V][3] (device, float32) and
+ * the loss gradient dL/dv[V][3] (device), writes
  *   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f)/|grad_x f|^2,
  * i.e. dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2 for a vertex that
- * stays on the level set f = 0.  Activations are recomputed at each vertex.
- * dL_dtheta is device float32, packed like the MLP blob's parameters, and is
- * overwritten.  Deterministic (fixed-order two-level reduction). */
+ * stays on the level set f = 0 (a rule the paper does not state; it follows
+ * from differentiating f(v(theta); theta) = 0).
+ * Neural SDB: dL_dtheta is packed like the MLP blob's parameters; the
+ *   activations are recomputed at each vertex.
+ * Analytic SDB: dL_dtheta is float32[n_prim][20], laid out like the
+ *   gh_csg_prim records: slots 2..4 hold dL/dcentre, 5..7 dL/dparam
+ *   (radius; major/minor radius; half sizes), every other slot 0 (rotations
+ *   are not differentiated).  Each vertex contributes to the one primitive the
+ *   min/max fold selects there.
+ * dL_dtheta is device float32 and is overwritten.  Deterministic
+ * (fixed-order reductions).  V = 0 gives zeros. */
 int gh_backward(const gh_sdb *sdb, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
                 void *stream);
 

@@ -80,6 +80,8 @@ def lib():
             L.or_grad_theta_point.argtypes = [P, P, P, I64]
             L.or_adjoint.restype = I
             L.or_adjoint.argtypes = [P, I64, P, P, P, I64]
+            L.or_csg_adjoint.restype = I
+            L.or_csg_adjoint.argtypes = [P, I64, P, P, P]
             L.or_num_threads.restype = I
             _lib = L
     return _lib
@@ -129,6 +131,11 @@ class SDB:
     def adjoint(self, verts, dldv) -> np.ndarray:
         v = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3)
         g = np.ascontiguousarray(dldv, dtype=np.float64).reshape(-1, 3)
+        if self.kind == "csg":
+            out = np.zeros((self.nprim, PRIM_STRIDE), np.float64)
+            if lib().or_csg_adjoint(self.h, v.shape[0], _ptr(v), _ptr(g), _ptr(out)) != 0:
+                raise ValueError("csg adjoint failed")
+            return out
         out = np.zeros(self.nparam, np.float64)
         if lib().or_adjoint(self.h, v.shape[0], _ptr(v), _ptr(g), _ptr(out), self.nparam) != 0:
             raise ValueError("adjoint needs a neural SDB")
@@ -141,7 +148,9 @@ def csg(prims) -> SDB:
     h = lib().or_csg_new(a.shape[0], _ptr(a))
     if not h:
         raise ValueError("empty CSG")
-    return SDB(h, "csg")
+    sdb = SDB(h, "csg")
+    sdb.nprim = a.shape[0]
+    return sdb
 
 
 def mlp_param_count(width: int, nmid: int) -> int:

@@ -796,6 +796,132 @@ int or_adjoint(const void *hs, int64_t nv, const double *v, const double *dldv, 
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint of an analytic (CSG) SDB                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * A min / max fold selects one primitive at each point (union keeps the
+ * running value unless the new distance is strictly smaller, subtraction and
+ * intersection unless it is strictly larger), so f = sgn * d_a(p) with
+ * sgn = -1 when the selected primitive was subtracted.  Gradients of the
+ * exact distances with respect to the point, the centre c (the negative of the
+ * point gradient) and the size parameters:
+ *   sphere  d = |p - c| - r:                 dd/dr = -1
+ *   torus   a = |(qx,qz)| - R, d = |(a,qy)| - r:  dd/dR = -a/|(a,qy)|, dd/dr = -1
+ *   box     e = |q| - h; outside: d = |max(e,0)|, dd/dh = -max(e,0)/d;
+ *           inside: d = max_k e_k, dd/dh_k = -1 for the largest k
+ * with q = Rot (p - c) and dd/dp = Rot^T dd/dq.
+ * Output per primitive (17 doubles like the primitive rows): dL/dc in slots
+ * 2..4, dL/dparam in slots 5..7, everything else 0.
+ */
+static double prim_grad(const double *pr, const double *p, double *gp /*dd/dp*/, double *gs /*dd/dparam*/) {
+    const double *c = pr + 2, *prm = pr + 5, *R = pr + 8;
+    double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]}, q[3], gq[3] = {0, 0, 0}, val;
+    for (int r = 0; r < 3; ++r) q[r] = R[3 * r] * d[0] + R[3 * r + 1] * d[1] + R[3 * r + 2] * d[2];
+    gs[0] = gs[1] = gs[2] = 0.0;
+    switch ((int)pr[0]) {
+    case OR_SPHERE: {
+        double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        val = n - prm[0];
+        for (int a = 0; a < 3; ++a) gq[a] = n > 0 ? q[a] / n : 0.0;
+        gs[0] = -1.0;
+        break;
+    }
+    case OR_TORUS: {
+        double rxz = sqrt(q[0] * q[0] + q[2] * q[2]);
+        double a = rxz - prm[0];
+        double n = sqrt(a * a + q[1] * q[1]);
+        val = n - prm[1];
+        if (n > 0) {
+            gq[0] = rxz > 0 ? a * q[0] / (rxz * n) : 0.0;
+            gq[1] = q[1] / n;
+            gq[2] = rxz > 0 ? a * q[2] / (rxz * n) : 0.0;
+            gs[0] = -a / n;
+        }
+        gs[1] = -1.0;
+        break;
+    }
+    default: {
+        double e[3], o2 = 0.0;
+        int km = 0;
+        for (int a = 0; a < 3; ++a) {
+            e[a] = fabs(q[a]) - prm[a];
+            if (e[a] > 0) o2 += e[a] * e[a];
+            if (e[a] > e[km]) km = a;
+        }
+        if (o2 > 0) {
+            double n = sqrt(o2);
+            val = n;
+            for (int a = 0; a < 3; ++a) {
+                double m = e[a] > 0 ? e[a] / n : 0.0;
+                gq[a] = (q[a] < 0 ? -1.0 : 1.0) * m;
+                gs[a] = -m;
+            }
+        } else {
+            val = e[km];
+            gq[km] = q[km] < 0 ? -1.0 : 1.0;
+            gs[km] = -1.0;
+        }
+        break;
+    }
+    }
+    for (int a = 0; a < 3; ++a) gp[a] = R[a] * gq[0] + R[3 + a] * gq[1] + R[6 + a] * gq[2];
+    return val;
+}
+
+int or_csg_adjoint(const void *hs, int64_t nv, const double *v, const double *dldv, double *out) {
+    const osdb *s = (const osdb *)hs;
+    if (s->kind != 0) return -1;
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    size_t np = (size_t)s->nprim * OR_PRIM_STRIDE;
+    double *acc = (double *)calloc((size_t)nth * np, sizeof(double));
+#pragma omp parallel num_threads(nth)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *mine = acc + (size_t)t * np;
+        int64_t a0 = nv * t / nth, a1 = nv * (t + 1) / nth;
+        for (int64_t qv = a0; qv < a1; ++qv) {
+            const double *p = v + 3 * qv;
+            int act = 0;
+            double sgn = 1.0, f = prim_eval(s->prim, p);
+            for (int n = 1; n < s->nprim; ++n) {
+                const double *pr = s->prim + (size_t)n * OR_PRIM_STRIDE;
+                double d = prim_eval(pr, p);
+                int op = (int)pr[1];
+                if (op == OR_UNION) {
+                    if (d < f) { f = d; act = n; sgn = 1.0; }
+                } else if (op == OR_SUBTRACT) {
+                    if (-d > f) { f = -d; act = n; sgn = -1.0; }
+                } else {
+                    if (d > f) { f = d; act = n; sgn = 1.0; }
+                }
+            }
+            double gp[3], gs[3];
+            prim_grad(s->prim + (size_t)act * OR_PRIM_STRIDE, p, gp, gs);
+            double gx[3] = {sgn * gp[0], sgn * gp[1], sgn * gp[2]};
+            double g2 = gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2];
+            if (!(g2 > 0)) continue;
+            double sv = -(dldv[3 * qv] * gx[0] + dldv[3 * qv + 1] * gx[1] + dldv[3 * qv + 2] * gx[2]) / g2;
+            double *o = mine + (size_t)act * OR_PRIM_STRIDE;
+            for (int a = 0; a < 3; ++a) {
+                o[2 + a] += sv * (-gx[a]);     /* df/dc = -sgn dd/dp */
+                o[5 + a] += sv * sgn * gs[a];
+            }
+        }
+    }
+    memset(out, 0, sizeof(double) * np);
+    for (int t = 0; t < nth; ++t)
+        for (size_t i = 0; i < np; ++i) out[i] += acc[(size_t)t * np + i];
+    free(acc);
+    return 0;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

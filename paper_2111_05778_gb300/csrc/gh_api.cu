@@ -969,12 +969,28 @@ extern "C" int gh_batch_graph_free(void *graph) {
 extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
                            void *stream) {
     gh_sdb *s = const_cast<gh_sdb *>(cs);
-    if (!s || s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "gh_backward needs a neural SDB");
+    if (!s) return fail(GH_ERR_ARG, "gh_backward: NULL sdb");
     if (V < 0 || V > (1ll << 31) - 1) return fail(GH_ERR_ARG, "gh_backward: V = %lld out of range", (long long)V);
     if (!dL_dtheta || (V > 0 && (!verts || !dL_dv))) return fail(GH_ERR_ARG, "gh_backward: NULL pointer");
     int dev, nsm, rc;
     if ((rc = ensure_device(&dev, &nsm))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (s->kind == GH_SDB_CSG) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const size_t need = (size_t)7 * (size_t)(V > 0 ? V : 1);
+        if (s->adj_floats < need) {
+            if (s->adj) cudaFree(s->adj);
+            s->adj = nullptr;
+            s->adj_floats = 0;
+            GH_CUDA(cudaMalloc((void **)&s->adj, sizeof(float) * need));
+            s->adj_floats = need;
+        }
+        int *act = reinterpret_cast<int *>(s->adj);
+        float *contrib = s->adj + (V > 0 ? V : 1);
+        csg_adjoint(s->d_prims, s->nprim, verts, dL_dv, (int)V, act, contrib, dL_dtheta, st);
+        GH_CUDA(cudaGetLastError());
+        return GH_OK;
+    }
     if (V == 0) {
         GH_CUDA(cudaMemsetAsync(dL_dtheta, 0, sizeof(float) * s->nparam, st));
         return GH_OK;

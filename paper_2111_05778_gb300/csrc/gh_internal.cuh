@@ -138,6 +138,8 @@ size_t adjoint_buffer_floats(int W, int n_mid, int VC, int splits);
 void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, float *grad, bool accumulate,
                    const AdjBuffers &b, cudaStream_t st);
 void adjoint_fill_ones(float *p, long long n, cudaStream_t st);
+void csg_adjoint(const Prim *prims, int nprim, const float *V, const float *dL, int nv, int *act, float *contrib,
+                 float *out, cudaStream_t st);
 
 // calibration helpers (k_pipeline.cu)
 void launch_rand_points(float *p, long long n, const float *lo, float ext, unsigned long long seed, cudaStream_t st);

@@ -238,4 +238,148 @@ void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, floa
 
 void adjoint_fill_ones(float *p, long long n, cudaStream_t st) { k_fill<<<256, 256, 0, st>>>(p, n, 1.f); }
 
+// ---------------------------------------------------------------------------
+// Adjoint of an analytic (CSG) SDB.  The min / max fold selects one
+// primitive a at each vertex (the running value is replaced only by a
+// strictly smaller union term or a strictly larger subtract / intersect
+// term), so f = sgn d_a with sgn = -1 for a subtracted primitive.  With
+// q = Rot (v - c):
+//   sphere  d = |q| - r                  dd/dq = q/|q|,  dd/dr = -1
+//   torus   a = |(qx,qz)| - R, d = |(a,qy)| - r
+//           dd/dq = (a qx/|(qx,qz)|, qy, a qz/|(qx,qz)|) / |(a,qy)|, dd/dR = -a/|(a,qy)|, dd/dr = -1
+//   box     e = |q| - h; outside: d = |max(e,0)|, dd/dq = sign(q) max(e,0)/d, dd/dh = -max(e,0)/d;
+//           inside: d = max_k e_k, dd/dq_k = sign(q_k), dd/dh_k = -1 (largest k)
+// dd/dv = Rot^T dd/dq and dd/dc = -dd/dv.  Each vertex contributes
+// s_v df/dtheta_a to its primitive a only.
+// ---------------------------------------------------------------------------
+__device__ float csg_prim_grad(const Prim &P, float x, float y, float z, float *gv, float *gs) {
+    const float dx = x - P.c[0], dy = y - P.c[1], dz = z - P.c[2];
+    const float *R = P.rot;
+    const float q0 = R[0] * dx + R[1] * dy + R[2] * dz;
+    const float q1 = R[3] * dx + R[4] * dy + R[5] * dz;
+    const float q2 = R[6] * dx + R[7] * dy + R[8] * dz;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, val;
+    gs[0] = gs[1] = gs[2] = 0.f;
+    if (P.type == GH_PRIM_SPHERE) {
+        const float n = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+        val = n - P.p[0];
+        if (n > 0.f) {
+            g0 = q0 / n;
+            g1 = q1 / n;
+            g2 = q2 / n;
+        }
+        gs[0] = -1.f;
+    } else if (P.type == GH_PRIM_TORUS) {
+        const float rxz = sqrtf(q0 * q0 + q2 * q2);
+        const float a = rxz - P.p[0];
+        const float n = sqrtf(a * a + q1 * q1);
+        val = n - P.p[1];
+        if (n > 0.f) {
+            g0 = rxz > 0.f ? a * q0 / (rxz * n) : 0.f;
+            g1 = q1 / n;
+            g2 = rxz > 0.f ? a * q2 / (rxz * n) : 0.f;
+            gs[0] = -a / n;
+        }
+        gs[1] = -1.f;
+    } else {
+        const float q[3] = {q0, q1, q2};
+        float e[3], o2 = 0.f, g[3] = {0.f, 0.f, 0.f};
+        int km = 0;
+        for (int k = 0; k < 3; ++k) {
+            e[k] = fabsf(q[k]) - P.p[k];
+            if (e[k] > 0.f) o2 += e[k] * e[k];
+            if (e[k] > e[km]) km = k;
+        }
+        if (o2 > 0.f) {
+            const float n = sqrtf(o2);
+            val = n;
+            for (int k = 0; k < 3; ++k) {
+                const float mk = e[k] > 0.f ? e[k] / n : 0.f;
+                g[k] = q[k] < 0.f ? -mk : mk;
+                gs[k] = -mk;
+            }
+        } else {
+            val = e[km];
+            g[km] = q[km] < 0.f ? -1.f : 1.f;
+            gs[km] = -1.f;
+        }
+        g0 = g[0];
+        g1 = g[1];
+        g2 = g[2];
+    }
+    gv[0] = R[0] * g0 + R[3] * g1 + R[6] * g2;
+    gv[1] = R[1] * g0 + R[4] * g1 + R[7] * g2;
+    gv[2] = R[2] * g0 + R[5] * g1 + R[8] * g2;
+    return val;
+}
+
+__device__ float csg_prim_val(const Prim &P, float x, float y, float z) {
+    float gv[3], gs[3];
+    return csg_prim_grad(P, x, y, z, gv, gs);
+}
+
+__global__ void k_csg_adj_vertex(const Prim *__restrict__ prims, int nprim, const float *__restrict__ V,
+                                 const float *__restrict__ dL, int nv, int *__restrict__ act,
+                                 float *__restrict__ contrib) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+        const float x = V[3 * v], y = V[3 * v + 1], z = V[3 * v + 2];
+        int a = 0;
+        float sgn = 1.f, f = csg_prim_val(prims[0], x, y, z);
+        for (int n = 1; n < nprim; ++n) {
+            const float d = csg_prim_val(prims[n], x, y, z);
+            const int op = prims[n].op;
+            if (op == GH_OP_UNION) {
+                if (d < f) { f = d; a = n; sgn = 1.f; }
+            } else if (op == GH_OP_SUBTRACT) {
+                if (-d > f) { f = -d; a = n; sgn = -1.f; }
+            } else {
+                if (d > f) { f = d; a = n; sgn = 1.f; }
+            }
+        }
+        float gv[3], gs[3];
+        csg_prim_grad(prims[a], x, y, z, gv, gs);
+        const float gx = sgn * gv[0], gy = sgn * gv[1], gz = sgn * gv[2];
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        const float sv = g2 > 0.f ? -(dL[3 * v] * gx + dL[3 * v + 1] * gy + dL[3 * v + 2] * gz) / g2 : 0.f;
+        act[v] = a;
+        float *o = contrib + (size_t)6 * v;
+        o[0] = -sv * gx;
+        o[1] = -sv * gy;
+        o[2] = -sv * gz;
+        o[3] = sv * sgn * gs[0];
+        o[4] = sv * sgn * gs[1];
+        o[5] = sv * sgn * gs[2];
+    }
+}
+
+// one block per primitive: fixed-order sums over the vertices it was active at
+__global__ void __launch_bounds__(256) k_csg_adj_reduce(const int *__restrict__ act, const float *__restrict__ contrib,
+                                                         int nv, float *__restrict__ out) {
+    __shared__ float red[6][256];
+    const int prim = blockIdx.x;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int v = threadIdx.x; v < nv; v += blockDim.x)
+        if (act[v] == prim)
+            for (int k = 0; k < 6; ++k) acc[k] += contrib[(size_t)6 * v + k];
+    for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 20) {
+        float val = 0.f;
+        if (threadIdx.x >= 2 && threadIdx.x < 8) val = red[threadIdx.x - 2][0];
+        out[(size_t)20 * prim + threadIdx.x] = val;
+    }
+}
+
+void csg_adjoint(const Prim *prims, int nprim, const float *V, const float *dL, int nv, int *act, float *contrib,
+                 float *out, cudaStream_t st) {
+    if (nv > 0) k_csg_adj_vertex<<<(nv + 255) / 256 < 4096 ? (nv + 255) / 256 : 4096, 256, 0, st>>>(
+        prims, nprim, V, dL, nv, act, contrib);
+    k_csg_adj_reduce<<<nprim, 256, 0, st>>>(act, contrib, nv, out);
+}
+
 }  // namespace gh

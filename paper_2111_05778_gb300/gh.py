@@ -420,17 +420,21 @@ def polygonize_csg_noalloc(prims_dev, n_prim, N, bufs: Buffers, lo=-1.0, hi=1.0,
     return rc
 
 
-def backward(sdb: "MlpSdb", verts, dl_dv, stream=None):
-    """gh_backward: dL/dtheta (packed like the MLP parameters) of a loss on mesh
-    vertices, through the implicit rule dv/dtheta = -grad f (df/dtheta)/|grad f|^2."""
+def backward(sdb: Sdb, verts, dl_dv, stream=None):
+    """gh_backward: dL/dtheta of a loss on mesh vertices through the implicit
+    rule dv/dtheta = -grad f (df/dtheta)/|grad f|^2.  Neural SDB: packed like
+    the MLP parameters.  Analytic SDB: [n_prim, 20] laid out like the
+    primitive records (centre gradient in columns 2..4, size-parameter
+    gradient in 5..7)."""
     import torch
 
     v = verts.detach().contiguous().to(torch.float32)
     g = dl_dv.detach().contiguous().to(torch.float32)
-    out = torch.empty(sdb.params.size, dtype=torch.float32, device=v.device)
+    n = sdb.params.size if isinstance(sdb, MlpSdb) else sdb.prims.shape[0] * 20
+    out = torch.empty(n, dtype=torch.float32, device=v.device)
     check(lib().gh_backward(sdb.handle, v.data_ptr(), g.data_ptr(), v.shape[0], out.data_ptr(),
                             _stream_ptr(stream)))
-    return out
+    return out if isinstance(sdb, MlpSdb) else out.reshape(-1, 20)
 
 
 def unique_vertices(mesh: "Mesh"):

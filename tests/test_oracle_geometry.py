@@ -112,3 +112,44 @@ def test_golden_sphere_counts_consistent():
     for r in rows[N <= 128]:
         hr = oracle.hop(s, int(r[0]))
         assert hr.col_evals.sum() == r[1] and hr.marks.size == r[2]
+
+
+def test_csg_adjoint_matches_implicit_fd():
+    """Adjoint of the analytic scene w.r.t. centres and size parameters
+    against central differences of the implicit loss (FP64, oracle evaluator
+    only): L(theta') with v(theta') = v - (f(v;theta') - f(v;theta)) grad f/|grad f|^2."""
+    prims = synth.csg_prims(5)
+    s = oracle.csg(prims)
+    N = 48
+    _, mr = oracle.polygonize(s, N)
+    keys, pos = mr.tri_keys.ravel(), mr.tri_pos.reshape(-1, 3)
+    _, first = np.unique(keys, return_index=True)
+    V = pos[first]
+    c = np.array([0.03, -0.02, 0.01])
+    r = np.linalg.norm(V - c, axis=1)
+    dldv = (2 * (r - 0.4) / r)[:, None] * (V - c) / V.shape[0]
+    g = s.adjoint(V, dldv)
+    f0 = s.eval(V)
+    h = 1e-7
+    gx = np.stack([(s.eval(V + h * e) - s.eval(V - h * e)) / (2 * h) for e in np.eye(3)], 1)
+    n2 = (gx * gx).sum(1)
+
+    def implicit_loss(pp):
+        f1 = oracle.csg(pp).eval(V)
+        v = V - ((f1 - f0) / n2)[:, None] * gx
+        return np.mean((np.linalg.norm(v - c, axis=1) - 0.4) ** 2)
+
+    d = 1e-7
+    checked = 0
+    for i in range(prims.shape[0]):
+        for slot in [2, 3, 4, 5, 6]:
+            if prims[i, 0] == synth.SPHERE and slot == 6:
+                continue
+            hi = prims.copy()
+            lo = prims.copy()
+            hi[i, slot] += d
+            lo[i, slot] -= d
+            fd = (implicit_loss(hi) - implicit_loss(lo)) / (2 * d)
+            assert abs(g[i, slot] - fd) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (i, slot, g[i, slot], fd)
+            checked += 1
+    assert checked > 100 and np.abs(g[:, 2:8]).max() > 0
