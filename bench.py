@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--N", type=int, default=None, help="grid size (default 1024; smaller for profiling)")
-    ap.add_argument("--workload", default="neural", choices=["neural", "batch"],
-                    help="neural: one N=1024 neural SDB (default); batch: the 64-item batch, graph-replayed")
+    ap.add_argument("--workload", default="neural", choices=["neural", "batch", "csg", "adjoint"],
+                    help="neural: one N=1024 neural SDB (default); batch: the 64-item batch, graph-replayed; "
+                         "csg: the analytic scene at N=512; adjoint: gh_backward on the N=256 neural mesh")
     args = ap.parse_args()
     if args.N:
         WORKLOAD["N"] = int(args.N)
@@ -445,12 +446,104 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, steps, warmup, flush, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+        flush.zero_()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        flush.zero_()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.mean(ts))
+
+
+def run_csg(args):
+    """The analytic scene (CSG seed 0: 24 spheres + 8 tori - 4 boxes) at N = 512, FP32."""
+    import torch
+
+    from paper_2111_05778_gb300 import gh, synth
+
+    torch.cuda.set_device(0)
+    N = args.N or 512
+    sdb = gh.CsgSdb(synth.csg_prims(0))
+    probe = gh.polygonize(sdb, N)
+    bufs = gh.Buffers(int(probe.n_tris * 1.05) + 4096)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    gh.set_profiling(True)
+    phases = {}
+
+    def step():
+        gh.polygonize_into(sdb, N, bufs, sync=False, stream=stream)
+        _, ph = gh.last_profile()
+        for k, v in ph.items():
+            phases.setdefault(k, []).append(v)
+
+    clocks = ClockSampler(0)
+    ms = _timed(step, args.steps, args.warmup, flush, stream)
+    clk = clocks.stop()
+    st = bufs.stats_dict()
+    line = {"metric": "surface cells/s", "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "analytic CSG seed 0 (24 spheres + 8 tori - 4 boxes), N=%d, [-1,1]^3" % N},
+            "ms_per_mesh": ms, "phases_ms": {k: float(np.mean(v[args.warmup:] or v)) for k, v in phases.items()},
+            "hop_evals": st["hop_evals"], "marked_cells": st["marked_cells"],
+            "unique_vertices": st["unique_vertices"], "surface_cells": st["surface_cells"],
+            "triangles": st["triangles"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """gh_backward for the C4 workload: the width-256 network of seed 1, its
+    N = 256 FP32 mesh, loss = mean over unique vertices of (|v - c| - 0.55)^2."""
+    import torch
+
+    from paper_2111_05778_gb300 import gh, synth
+
+    torch.cuda.set_device(0)
+    W, N = 256, args.N or 256
+    sdb = gh.MlpSdb(synth.mlp_params(1, W), W)
+    verts, faces, _ = gh.unique_vertices(gh.polygonize(sdb, N, keys=True))
+    c = torch.tensor(np.random.default_rng(4).uniform(-0.05, 0.05, 3), dtype=torch.float32, device="cuda")
+    v = verts.clone().requires_grad_(True)
+    loss = ((v - c).norm(dim=1) - 0.55).pow(2).mean()
+    loss.backward()
+    dldv = v.grad.detach()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = _timed(lambda: gh.backward(sdb, verts, dldv), args.steps, args.warmup, flush, stream)
+    V = verts.shape[0]
+    flop = V * 2 * (3 * W + 5 * W * W + W) * 3  # forward, delta chain, weight sums (weights only)
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
+    line = {"metric": "adjoint vertices/s", "value": V / (ms / 1e3), "unit": "vertices/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "implicit adjoint, neural SDB seed 1 width 256, N=%d mesh, %d vertices" % (N, V)},
+            "roofline": {"bound": "alu", "achieved": flop / (ms / 1e3) / 1e12, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": flop / (ms / 1e3) / 1e12 / fp32_peak, "traffic": None,
+                         "kernel": "gh_backward (all kernels)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "csg":
+        run_csg(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
