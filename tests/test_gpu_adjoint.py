@@ -124,7 +124,11 @@ def test_csg_adjoint_matches_oracle_and_finite_differences():
 
     rng = np.random.default_rng(21)
     pairs = [(int(i), int(sl)) for i, sl in zip(rng.integers(0, prims.shape[0], 32), rng.integers(2, 7, 32))]
-    d = 1e-4
+    # the loss is piecewise smooth: the exact box distance has a kink on the
+    # box's medial set and the fold switches primitive where two distances
+    # tie; a 1e-4 step (1/200 of a cell) crosses such a set at some vertices,
+    # so the analytic check uses 1e-6
+    d = 1e-6
     for i, sl in pairs:
         hi = prims.copy()
         lo = prims.copy()
