@@ -603,6 +603,8 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         if (s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "GH_BF16_REFINE applies to neural SDBs only");
         if (!bf16_supported(s->mlp.width))
             return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path not available for width %d", s->mlp.width);
+        if (s->mlp.n_mid > bf16_max_mid())
+            return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path supports at most %d hidden layers", bf16_max_mid());
         const float eps = o.eps >= 0.f ? o.eps : s->eps;
         if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "BF16 path needs eps: pass opts.eps or call gh_sdb_calibrate");
         g.eps = eps;
@@ -653,7 +655,8 @@ extern "C" int gh_eval(const gh_sdb *s, const float *p, int64_t n, float *out, i
     } else if (precision == GH_FP32) {
         launch_eval_points_mlp_fp32(s->mlp, p, n, out, nsm, st);
     } else if (precision == GH_BF16_REFINE) {
-        if (!bf16_supported(s->mlp.width)) return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width");
+        if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid())
+            return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width / depth");
         launch_eval_points_mlp_bf16(s->mlp, p, n, out, nsm, st);
     } else {
         return fail(GH_ERR_ARG, "unknown precision %d", precision);
@@ -820,6 +823,9 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
         if ((rc = check_grid(&grids[b], &P.g[b], o.tau_mode))) return rc;
         if ((rc = check_mesh(&outs[b]))) return rc;
         if (sd[b]->kind == GH_SDB_MLP && o.precision == GH_BF16_REFINE) {
+            if (sd[b]->mlp.n_mid > bf16_max_mid())
+                return fail(GH_ERR_UNIMPLEMENTED, "item %d: BF16 path supports at most %d hidden layers", b,
+                            bf16_max_mid());
             const float eps = o.eps >= 0.f ? o.eps : sd[b]->eps;
             if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "item %d: BF16 needs eps (calibrate the SDB)", b);
             P.g[b].eps = eps;

@@ -40,15 +40,18 @@ constexpr int CTL_STOP = 1, CTL_ABORT = 2;
 
 enum { MODE_HOP = 0, MODE_VERTS = 1, MODE_POINTS = 2 };
 
+constexpr int MAXMID = 8;  // hidden layers supported by the tensor-core engine
+
 template <int W>
 struct SmemB {
-    uint8_t a[2][W / 64][TM * 128];  // A operands: up to 2 tiles, K-blocks of 128 rows x 128 B (1024-aligned)
+    uint8_t a[2][W / 64][TM * 128];  // A operands: one per tile, K-blocks of 128 rows x 128 B (1024-aligned)
     uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
-    float4 w0b[W];                   // layer 0: W0 row and bias
-    float bmid[16 * W];              // hidden-layer biases (n_mid <= 16)
-    float wout[W];                   // output-layer weights
-    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full, a_full, drain, item_ready;
-    const uint16_t *cur_wbf;  // weights of the item being processed
+    float4 w0b[2][W];                // per tile: layer-0 rows and biases of its current item
+    float bmid[2][MAXMID * W];       // per tile: hidden-layer biases
+    float wout[2][W];                // per tile: output-layer weights
+    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2], a_full[2], item_ready[2], drain;
+    const uint16_t *cur_wbf[2];      // per tile: weights of its current item
+    int done[2];                     // per tile: no more work
     uint32_t tmem_base;
     int ctl;
 };
@@ -179,17 +182,16 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-// OR-reduction over the NT epilogue threads (named barrier 1).
-template <int NT>
-__device__ __forceinline__ bool epi_any(bool v) {
+// OR-reduction over the 128 epilogue threads of one tile (named barrier id).
+__device__ __forceinline__ bool epi_any(int id, bool v) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "bar.red.or.pred q, %2, 128, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)v), "n"(NT)
+        : "r"((uint32_t)v), "r"(id)
         : "memory");
     return out != 0;
 }
@@ -200,17 +202,19 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, floa
 }
 
 // ---------------------------------------------------------------------------
-// TILES 128-row tiles per CTA (M = 128 * TILES rows per weight K-block).
-// A batch of items is walked in order: every CTA takes rows (rays or points)
-// from the shared per-item queues of item `cur`; when the item has no work
-// left for it, the CTA moves to the next item (reloading layer 0; the producer
-// reads the item's weights at the start of every step).
+// TILES 128-row tiles per CTA.  With two tiles the tensor core alternates
+// between them (ping-pong): while tile 0's epilogue warps turn layer l into
+// layer l+1's operand, the MMAs of tile 1's layer l run, and the other way
+// round.  Each tile walks the items of the batch on its own: its rows take
+// rays (or points) from item cur's queue, and when the item has no work left
+// for the tile it moves to the next one, reloading its layer-0 weights,
+// biases and output weights; the producer streams the weights of whichever
+// item the phase's tile is on.
 template <int W, int MODE, int TILES>
 __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     k_mlp_bf16(const Item *__restrict__ items, int n_items, const float *__restrict__ pts, long long npts,
                float *__restrict__ outv) {
     extern __shared__ uint8_t smem_raw[];
-    constexpr int NEPI = 128 * TILES;
     constexpr int KB = W / 64;
     constexpr uint32_t STAGE_BYTES = W * 128;
     constexpr uint32_t TMEM_COLS = TILES * W < 32 ? 32 : TILES * W;
@@ -224,23 +228,30 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     // ---- set-up ----------------------------------------------------------
     {
         const MlpDev &m0 = items[0].m;
-        if (tid < W) {
-            sm.w0b[tid] = make_float4(m0.w0[3 * tid], m0.w0[3 * tid + 1], m0.w0[3 * tid + 2], m0.b0[tid]);
-            sm.wout[tid] = m0.wout[tid];
+        for (int i = tid; i < TILES * W; i += blockDim.x) {
+            const int t = i / W, o = i - t * W;
+            sm.w0b[t][o] = make_float4(m0.w0[3 * o], m0.w0[3 * o + 1], m0.w0[3 * o + 2], m0.b0[o]);
+            sm.wout[t][o] = m0.wout[o];
         }
-        for (int i = tid; i < n_mid * W; i += blockDim.x) sm.bmid[i] = m0.bm[i];
+        for (int i = tid; i < TILES * n_mid * W; i += blockDim.x) {
+            const int t = i / (n_mid * W), r = i - t * (n_mid * W);
+            sm.bmid[t][r] = m0.bm[r];
+        }
     }
     if (tid == 0) {
         for (int i = 0; i < NSTAGE; ++i) {
             mbar_init(&sm.full[i], 1);
             mbar_init(&sm.empty[i], 1);
         }
-        mbar_init(&sm.acc_full, 1);
-        mbar_init(&sm.a_full, NEPI);
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(&sm.acc_full[t], 1);
+            mbar_init(&sm.a_full[t], 128);
+            mbar_init(&sm.item_ready[t], 1);
+            sm.cur_wbf[t] = items[0].m.wbf;
+            sm.done[t] = t < TILES ? 0 : 1;
+        }
         mbar_init(&sm.drain, 1);
-        mbar_init(&sm.item_ready, 1);
         sm.ctl = 0;
-        sm.cur_wbf = items[0].m.wbf;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -253,29 +264,45 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
+    volatile int *vdone = sm.done;
 
     if (warp == 0) {
-        // ---- TMA producer: the weights of the current item, step after step --
+        // ---- TMA producer: the phases in the MMA's order ----------------------
         if (lane == 0) {
-            const int nblk = n_mid * KB;
             long long issued = 0;
-            uint32_t pi = 0;
+            int t = 0, lt[2] = {0, 0};
+            bool fin[2] = {false, TILES < 2};
+            uint32_t pir[2] = {0u, 0u};
+            const uint8_t *src[2] = {nullptr, nullptr};
             bool go = true;
-            while (go) {
-                if (!wait_bar(&sm.item_ready, pi, ctl, CTL_STOP | CTL_ABORT, ctr0)) break;
-                pi ^= 1u;
-                const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf);
-                for (int blk = 0; blk < nblk; ++blk) {
+            while (go && !(fin[0] && fin[1])) {
+                if (fin[t]) {
+                    t ^= 1;
+                    continue;
+                }
+                if (lt[t] == 0) {  // a new step of tile t: its item (or its end) is decided first
+                    if (!wait_bar(&sm.item_ready[t], pir[t], ctl, CTL_ABORT, ctr0)) break;
+                    pir[t] ^= 1u;
+                    if (vdone[t]) {
+                        fin[t] = true;
+                        if (!fin[t ^ 1]) t ^= 1;
+                        continue;
+                    }
+                    src[t] = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf[t]);
+                }
+                for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(issued % NSTAGE);
                     const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
-                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_STOP | CTL_ABORT, ctr0)) {
+                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0)) {
                         go = false;
                         break;
                     }
                     mbar_expect_tx(&sm.full[st], STAGE_BYTES);
-                    bulk_g2s(sm.w[st], wsrc + (size_t)blk * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
+                    bulk_g2s(sm.w[st], src[t] + (size_t)(lt[t] * KB + kb) * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
                     ++issued;
                 }
+                lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
+                if (!fin[t ^ 1]) t ^= 1;
             }
             // the copies still in flight land before the CTA may exit
             for (long long i = issued - NSTAGE; i < issued; ++i) {
@@ -285,40 +312,46 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- MMA issuer --------------------------------------------------------
+        // ---- MMA issuer: alternates between the tiles that still have work -----
         if (lane == 0) {
-            const uint32_t a0 = su32(&sm.a[0][0][0]), a1 = su32(&sm.a[TILES - 1][0][0]);
             long long consumed = 0;
-            uint32_t pa = 0;
+            int t = 0, lt[2] = {0, 0};
+            bool fin[2] = {false, TILES < 2};
+            uint32_t pa[2] = {0u, 0u};
             bool go = true;
-            while (go) {
-                for (int l = 0; l < n_mid && go; ++l) {
-                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, ctr0) || (*ctl & CTL_STOP)) {
+            while (go && !(fin[0] && fin[1])) {
+                if (fin[t]) {
+                    t ^= 1;
+                    continue;
+                }
+                if (!wait_bar(&sm.a_full[t], pa[t], ctl, CTL_ABORT, ctr0)) break;
+                pa[t] ^= 1u;
+                if (lt[t] == 0 && vdone[t]) {
+                    fin[t] = true;
+                    if (!fin[t ^ 1]) t ^= 1;
+                    continue;
+                }
+                tc_fence_after();
+                const uint32_t at = su32(&sm.a[t][0][0]);
+                for (int kb = 0; kb < KB; ++kb) {
+                    const int st = (int)(consumed % NSTAGE);
+                    if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0)) {
                         go = false;
                         break;
                     }
-                    pa ^= 1u;
                     tc_fence_after();
-                    for (int kb = 0; kb < KB; ++kb) {
-                        const int st = (int)(consumed % NSTAGE);
-                        if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0)) {
-                            go = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t wb = su32(sm.w[st]);
+                    const uint32_t wb = su32(sm.w[st]);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const unsigned long long bd = sdesc(wb + k * 32);
-                            umma(tmem, sdesc(a0 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
-                            if (TILES == 2)
-                                umma(tmem + W, sdesc(a1 + kb * (TM * 128) + k * 32), bd, IDESC, (kb | k) != 0);
-                        }
-                        umma_commit(&sm.empty[st]);
-                        ++consumed;
-                    }
-                    if (go) umma_commit(&sm.acc_full);
+                    for (int k = 0; k < 4; ++k)
+                        umma(tmem + (uint32_t)(t * W), sdesc(at + kb * (TM * 128) + k * 32), sdesc(wb + k * 32),
+                             IDESC, (kb | k) != 0);
+                    umma_commit(&sm.empty[st]);
+                    ++consumed;
                 }
+                if (!go) break;
+                umma_commit(&sm.acc_full[t]);
+                lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
+                if (!fin[t ^ 1]) t ^= 1;
             }
             // every MMA issued above has completed before TMEM is released
             umma_commit(&sm.drain);
@@ -326,8 +359,9 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         }
         __syncwarp();
     } else if (warp >= 4) {
-        // ---- epilogue: one row per thread ------------------------------------
-        const int et = tid - EPI_T0, t = et >> 7, row = et & (TM - 1), q = (warp - 4) & 3;
+        // ---- epilogue: one row per thread, 128 rows per tile -------------------
+        const int t = (warp - 4) >> 2, row = tid - EPI_T0 - 128 * t, q = (warp - 4) & 3;
+        const int bar = 1 + t;
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * W);
         const uint32_t arow = su32(&sm.a[t][0][0]) + (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
         const int sw = row & 7;
@@ -340,6 +374,9 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         float x = 0.f, y = 0.f;
         unsigned long long evals = 0, idx = 0;
         uint32_t pacc = 0;
+        float4 *w0b = sm.w0b[t];
+        float *bmid = sm.bmid[t];
+        float *wout = sm.wout[t];
         for (;;) {
             // 1. the work of this row, from item cur
             const GridP &g = it->g;
@@ -402,14 +439,19 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 }
             }
             __syncwarp();
-            const bool any = epi_any<NEPI>(live);
+            const bool any = epi_any(bar, live);
             // the abort decision goes through the barrier so that it is uniform
-            if (epi_any<NEPI>((*ctl & CTL_ABORT) != 0)) {
-                mbar_arrive(&sm.a_full);
+            if (epi_any(bar, (*ctl & CTL_ABORT) != 0)) {
+                if (row == 0) {
+                    vdone[t] = 1;
+                    __threadfence_block();
+                    mbar_arrive(&sm.item_ready[t]);
+                }
+                mbar_arrive(&sm.a_full[t]);
                 break;
             }
             if (!any) {
-                // item cur has no work left for this CTA: next item, or stop
+                // item cur has no work left for this tile: next item, or done
                 if (MODE == MODE_HOP) {
                     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
                     if (lane == 0 && evals) atomicAdd(&it->s.ctr->hop_evals, evals);
@@ -417,12 +459,12 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 }
                 ++cur;
                 if (cur >= n_items) {
-                    if (et == 0) {
-                        *ctl |= CTL_STOP;
+                    if (row == 0) {
+                        vdone[t] = 1;
                         __threadfence_block();
+                        mbar_arrive(&sm.item_ready[t]);
                     }
-                    epi_any<NEPI>(false);  // the stop bit is written before anyone arrives
-                    mbar_arrive(&sm.a_full);
+                    mbar_arrive(&sm.a_full[t]);  // the tile's final phase: the MMA sees done
                     break;
                 }
                 it = &items[cur];
@@ -430,18 +472,18 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 done = false;
                 {
                     const MlpDev &mm = it->m;
-                    for (int o = et; o < W; o += NEPI) {
-                        sm.w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
-                        sm.wout[o] = mm.wout[o];
+                    for (int o = row; o < W; o += 128) {
+                        w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+                        wout[o] = mm.wout[o];
                     }
-                    for (int i = et; i < n_mid * W; i += NEPI) sm.bmid[i] = mm.bm[i];
+                    for (int i = row; i < n_mid * W; i += 128) bmid[i] = mm.bm[i];
                 }
-                epi_any<NEPI>(false);  // layer-0 weights of the new item in place
+                epi_any(bar, false);  // the new item's parameters are in place
                 continue;
             }
-            if (et == 0) {
-                sm.cur_wbf = it->m.wbf;
-                mbar_arrive(&sm.item_ready);
+            if (row == 0) {
+                sm.cur_wbf[t] = it->m.wbf;
+                mbar_arrive(&sm.item_ready[t]);
             }
             const MlpDev &m = it->m;
             // 2. layer 0 (FP32) -> A operand
@@ -450,7 +492,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float4 w0 = sm.w0b[o + 2 * e], w1 = sm.w0b[o + 2 * e + 1];
+                    const float4 w0 = w0b[o + 2 * e], w1 = w0b[o + 2 * e + 1];
                     const float z0 = fmaf(w0.x, px, fmaf(w0.y, py, fmaf(w0.z, pz, w0.w)));
                     const float z1 = fmaf(w1.x, px, fmaf(w1.y, py, fmaf(w1.z, pz, w1.w)));
                     pk[e] = pack_relu_bf16(z0, z1);
@@ -459,15 +501,15 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 sts128(arow + kb * (TM * 128) + ((c ^ sw) << 4), pk[0], pk[1], pk[2], pk[3]);
             }
             fence_async_smem();
-            mbar_arrive(&sm.a_full);
+            mbar_arrive(&sm.a_full[t]);
             // 3. hidden layers
             float gsum = 0.f;
             for (int l = 0; l < n_mid; ++l) {
-                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, ctr0);
+                wait_bar(&sm.acc_full[t], pacc, ctl, CTL_ABORT, ctr0);
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
-                const float *bl = sm.bmid + l * W;
+                const float *bl = bmid + l * W;
                 uint32_t ra[32], rb[32];
                 tmem_ld32_async(taddr, ra);
                 tmem_wait_ld();
@@ -497,7 +539,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     }
                     tc_fence_before();
                     fence_async_smem();
-                    mbar_arrive(&sm.a_full);
+                    mbar_arrive(&sm.a_full[t]);
                 } else {
                     // output layer in FP32 from the accumulators
 #pragma unroll
@@ -506,7 +548,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                         uint32_t(&nx)[32] = (j & 1) ? ra : rb;
                         if (j + 1 < W / 32) tmem_ld32_async(taddr + 32 * (j + 1), nx);
                         const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
-                        const float4 *wp = reinterpret_cast<const float4 *>(sm.wout + 32 * j);
+                        const float4 *wp = reinterpret_cast<const float4 *>(wout + 32 * j);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             const float4 b = bp[c], w = wp[c];
@@ -607,6 +649,7 @@ void launch_bf16(const Item *items, int n_items, const float *p, long long n, fl
     }
 
 bool bf16_supported(int width) { return width == 64 || width == 128 || width == 256; }
+int bf16_max_mid() { return MAXMID; }
 
 #define GH_BF16_T(T, ...)                                \
     if ((T) == 1) { constexpr int TT = 1; __VA_ARGS__; } \
