@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--N", type=int, default=None, help="grid size (default 1024; smaller for profiling)")
-    ap.add_argument("--workload", default="neural", choices=["neural", "batch", "csg", "adjoint"],
+    ap.add_argument("--workload", default="neural", choices=["neural", "batch", "csg", "adjoint", "crossover"],
                     help="neural: one N=1024 neural SDB (default); batch: the 64-item batch, graph-replayed; "
                          "csg: the analytic scene at N=512; adjoint: gh_backward on the N=256 neural mesh")
     args = ap.parse_args()
@@ -534,8 +534,46 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_crossover(args):
+    """Grid hopping against enumeration (Sec. 2: every lattice point and cell)
+    on the same GPU, for the analytic scene and the width-256 network, over N
+    (the paper's Sec. 5 comparison, here with both methods on the GB300)."""
+    import torch
+
+    from paper_2111_05778_gb300 import gh, synth
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    cases = [("csg", gh.CsgSdb(synth.csg_prims(0)), (64, 128, 256, 512, 1024)),
+             ("mlp256", gh.MlpSdb(synth.mlp_params(1, 256), 256), (64, 128, 256, 512))]
+    for name, sdb, Ns in cases:
+        for N in Ns:
+            res = {"sdb": name, "N": N}
+            variants = [("hop_fp32", "fp32", "hop"), ("enum_fp32", "fp32", "enum")]
+            if name != "csg":
+                variants.insert(1, ("hop_bf16", "bf16", "hop"))
+            for key, prec, meth in variants:
+                eps = sdb.calibrate(N, n_points=1 << 18) if prec == "bf16" else None
+                probe = gh.polygonize(sdb, N, precision=prec, eps=eps, method=meth)
+                bufs = gh.Buffers(int(probe.n_tris * 1.05) + 4096)
+                gh.polygonize_into(sdb, N, bufs, precision=prec, eps=eps, method=meth)
+                ms = _timed(lambda: gh.polygonize_into(sdb, N, bufs, precision=prec, eps=eps, sync=False,
+                                                       stream=stream, method=meth),
+                            max(1, args.steps // 2), 1, flush, stream)
+                res[key + "_ms"] = ms
+                res[key + "_evals"] = bufs.stats_dict()["hop_evals"]
+            rows.append(res)
+            print(json.dumps(res), flush=True)
+    print(json.dumps({"workload": "crossover", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "crossover":
+        run_crossover(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

@@ -123,7 +123,12 @@ typedef struct {
                        /* (128, 256 or 512; 0 = 256)                          */
     int32_t mlp_tiles; /* tuning: 128-row tiles per CTA of the BF16 engine    */
                        /* (1 or 2; 0 = 2)                                     */
+    int32_t method;    /* GH_METHOD_HOP (Algorithm 1, default) or             */
+                       /* GH_METHOD_ENUM: f at all (N+1)^3 lattice points and */
+                       /* Marching Cubes on all N^3 cells (Sec. 2), FP32 only */
 } gh_options;
+#define GH_METHOD_HOP 0
+#define GH_METHOD_ENUM 1
 
 /* Counters written by the device (all int64 so a caller may read the struct
  * with one copy). */

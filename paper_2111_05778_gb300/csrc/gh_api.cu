@@ -393,7 +393,7 @@ extern "C" int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out) {
 static void free_scratch(gh_sdb *s) {
     Scratch &c = s->scr;
     void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist};
+                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->scr = Scratch{};
@@ -418,7 +418,12 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     const int NN = grid_ok ? s->scr_N : N;
     long long cm = c.cap_marks > want_marks ? c.cap_marks : want_marks;
     long long cv = c.cap_verts > want_verts ? c.cap_verts : want_verts;
+    float *keep_lat = c.lat;
+    const long long keep_cap = c.cap_lat;
+    c.lat = nullptr;
     free_scratch(s);
+    c.lat = keep_lat;
+    c.cap_lat = keep_cap;
     const long long ncols = (long long)NN * NN, nlines = (long long)(NN + 1) * (NN + 1);
     GH_CUDA(cudaMalloc((void **)&c.ctr, sizeof(Counters)));
     GH_CUDA(cudaMalloc((void **)&c.marks_raw, sizeof(unsigned long long) * cm));
@@ -435,6 +440,19 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     c.cap_marks = cm;
     c.cap_verts = cv;
     s->scr_N = NN;
+    return GH_OK;
+}
+
+// The dense lattice array of the enumeration method.
+static int ensure_lattice(gh_sdb *s, int N) {
+    const long long need = (long long)(N + 1) * (N + 1) * (N + 1);
+    if (s->scr.cap_lat >= need) return GH_OK;
+    if (s->scr.lat) cudaFree(s->scr.lat);
+    s->scr.lat = nullptr;
+    s->scr.cap_lat = 0;
+    GH_CUDA(cudaMalloc((void **)&s->scr.lat, sizeof(float) * need));
+    s->scr.cap_lat = need;
+    s->item_valid = false;
     return GH_OK;
 }
 
@@ -547,6 +565,20 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
     const int tiles = o.mlp_tiles == 1 ? 1 : 2;
     mark_phase(0, st);
     launch_init(c, st);
+    if (o.method == GH_METHOD_ENUM) {
+        // Sec. 2 enumeration: every lattice point, every cell
+        if (s->kind == GH_SDB_CSG) launch_lattice_csg(s->d_prims, s->nprim, g, c, st);
+        else launch_lattice_mlp_fp32(s->d_item, s->mlp.width, nsm, st);
+        launch_enum_stats(g, c, st);
+        for (int p = 1; p <= 5; ++p) mark_phase(p, st);
+        launch_mc_dense(g, c, out, nsm, st);
+        launch_finalize(c, out, (long long)g.N * g.N, st);
+        mark_phase(6, st);
+        g_prof.recorded = g_prof.enabled;
+        g_prof.launches = 5;
+        GH_CUDA(cudaGetLastError());
+        return GH_OK;
+    }
     if (s->kind == GH_SDB_CSG) {
         launch_hop_csg(s->d_item, 1, s->nprim, nsm, o.ray_block, st);
         mark_phase(1, st);
@@ -591,12 +623,15 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
                              void *stream) {
     gh_sdb *s = const_cast<gh_sdb *>(csdb);
     if (!s) return fail(GH_ERR_ARG, "NULL sdb");
-    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0};
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0, GH_METHOD_HOP};
     if (opts) o = *opts;
     GridP g;
     int rc = check_grid(grid, &g, o.tau_mode);
     if (rc) return rc;
     if ((rc = check_mesh(out))) return rc;
+    if (o.method != GH_METHOD_HOP && o.method != GH_METHOD_ENUM) return fail(GH_ERR_ARG, "unknown method %d", o.method);
+    if (o.method == GH_METHOD_ENUM && o.precision != GH_FP32)
+        return fail(GH_ERR_UNIMPLEMENTED, "the enumeration method runs in FP32 only");
     if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
         return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
     if (o.precision == GH_BF16_REFINE) {
@@ -619,6 +654,7 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
     long long want_v = 2 * want_m;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = ensure_scratch(s, g.N, want_m, want_v))) return rc;
+        if (o.method == GH_METHOD_ENUM && (rc = ensure_lattice(s, g.N))) return rc;
         if ((rc = enqueue_once(s, g, o, *out, nsm, st))) return rc;
         if (!o.sync) return GH_OK;
         Counters c;
@@ -805,10 +841,11 @@ static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_
 extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *const *sdbs, const gh_options *opts,
                                    gh_mesh *outs, void *stream, void **graph) {
     if (B < 1 || !grids || !sdbs || !outs) return fail(GH_ERR_ARG, "gh_polygonize_batch: empty or NULL arguments");
-    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0};
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0, GH_METHOD_HOP};
     if (opts) o = *opts;
     if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
         return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
+    if (o.method != GH_METHOD_HOP) return fail(GH_ERR_UNIMPLEMENTED, "batches run grid hopping only");
     int dev, nsm, rc;
     if ((rc = ensure_device(&dev, &nsm))) return rc;
     std::vector<gh_sdb *> sd(B);

@@ -81,6 +81,8 @@ struct Scratch {
     uint8_t *vflag;                 // [cap_verts] refinement flags
     uint32_t *rlist;                // [cap_verts] vertices to refine
     long long cap_marks, cap_verts;
+    float *lat;                     // enumeration: f at all (N+1)^3 lattice points
+    long long cap_lat;
 };
 
 // One polygonization of a batch: grid, scratch and SDB.  Kernels that serve
@@ -110,6 +112,9 @@ void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,
                               cudaStream_t st);
 void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
+void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, cudaStream_t st);
+void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
+void launch_enum_stats(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st);
 void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long long n, float *out,
                             cudaStream_t st);
@@ -120,6 +125,7 @@ void launch_eval_vertices_mlp_fp32(const Item *items, int n_items, int width, in
                                    cudaStream_t st);
 void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
+void launch_lattice_mlp_fp32(const Item *items, int width, int nsm, cudaStream_t st);
 
 // neural SDB, BF16 on tcgen05 tensor cores (k_mlp_bf16.cu)
 bool bf16_supported(int width);

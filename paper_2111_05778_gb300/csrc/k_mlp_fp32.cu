@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
 
 // Point lists over a batch of items: MODE 0 = the unique lattice vertices of
 // each item, MODE 1 = each item's refinement list, MODE 2 = explicit points
-// (one item).
+// (one item), MODE 3 = all (N+1)^3 lattice points into s.lat (enumeration).
 template <int W, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__ items, int n_items,
                                                          const float *pts, long long npts, float *outv) {
@@ -285,7 +285,10 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
         unsigned long long *counter = MODE == 1 ? &s.ctr->next_tile2 : &s.ctr->next_tile;
         if (tid == 0) {
             const bool stopped = MODE != 2 && (s.ctr->flags & STOP_FLAGS);
-            total_s = stopped ? 0ull : (MODE == 0 ? s.ctr->verts : (MODE == 1 ? s.ctr->refine : (unsigned long long)npts));
+            const unsigned long long nl = (unsigned long long)(g.N + 1) * (g.N + 1) * (g.N + 1);
+            total_s = stopped ? 0ull
+                              : (MODE == 0 ? s.ctr->verts
+                                           : (MODE == 1 ? s.ctr->refine : (MODE == 3 ? nl : (unsigned long long)npts)));
             tile_s = total_s ? atomicAdd(counter, 1ull) : 0ull;
         }
         __syncthreads();
@@ -301,6 +304,11 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
             if (r < total) {
                 if (MODE == 2) {
                     p = make_float4(pts[3 * r], pts[3 * r + 1], pts[3 * r + 2], 0.f);
+                } else if (MODE == 3) {
+                    const unsigned long long N1 = g.N + 1;
+                    const unsigned long long a = r % N1, b = (r / N1) % N1, c = r / (N1 * N1);
+                    p = make_float4(fmaf((float)a, g.h, g.lo[0]), fmaf((float)b, g.h, g.lo[1]),
+                                    fmaf((float)c, g.h, g.lo[2]), 0.f);
                 } else {
                     const unsigned long long key = s.vkey[MODE == 1 ? (unsigned long long)s.rlist[r] : r];
                     const int N1 = g.N + 1;
@@ -321,6 +329,7 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
                 if (MODE != 2 && !isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
                 if (MODE == 0) s.vval[r] = f;
                 else if (MODE == 1) s.vval[s.rlist[r]] = f;
+                else if (MODE == 3) s.lat[r] = f;
                 else outv[r] = f;
             }
         }
@@ -364,6 +373,14 @@ void launch_eval_vertices_mlp_fp32(const Item *items, int n_items, int width, in
             const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 0>, smem, nsm);
             k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr);
         }
+    })
+}
+
+void launch_lattice_mlp_fp32(const Item *items, int width, int nsm, cudaStream_t st) {
+    GH_DISPATCH_W(width, {
+        const size_t smem = sizeof(Smem<WW>);
+        const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 3>, smem, nsm);
+        k_pts_mlp_fp32<WW, 3><<<grid, NT, smem, st>>>(items, 1, nullptr, 0, nullptr);
     })
 }
 

@@ -435,20 +435,99 @@ __device__ __forceinline__ uint32_t find_c(const unsigned long long *__restrict_
     return lo;
 }
 
-__global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
-    if (s.ctr->flags & STOP_FLAGS) return;
-    const unsigned long long M = s.ctr->marks;
+// Case index, triangle table and warp prefix-sum emit of one cell per lane;
+// every lane of the warp calls it (valid == false for lanes without a cell).
+__device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const gh_mesh &out, bool valid, int i, int j,
+                                           int k, const float (&fv)[8]) {
     const int N = g.N, N1 = N + 1;
     const unsigned long long N13 = (unsigned long long)N1 * N1 * N1;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    int cs = 0;
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cs |= (fv[b] < 0.f) << b;
+    }
+    const bool surf = valid && cs != 0 && cs != 255;
+    const int nt = surf ? c_tab_n[cs] : 0;
+    // warp-exclusive prefix sum of the triangle counts, one atomic per warp
+    int x = nt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    const int wtot = __shfl_sync(FULL, x, 31);
+    unsigned long long tbase = 0;
+    if (wtot) {
+        if (lane == 31) tbase = atomicAdd(&ctr->tris, (unsigned long long)wtot);
+        tbase = __shfl_sync(FULL, tbase, 31);
+    }
+    tbase += (unsigned long long)(x - nt);
+    const unsigned sm = __ballot_sync(FULL, surf);
+    if (sm && out.cell_ids) {
+        unsigned long long cbase = 0;
+        if (lane == 0) cbase = atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
+        cbase = __shfl_sync(FULL, cbase, 0);
+        if (surf) {
+            const unsigned long long ci = cbase + __popc(sm & lt);
+            if (ci < (unsigned long long)out.capacity_cells) {
+                out.cell_ids[ci] = ((unsigned long long)i * N + j) * N + k;
+                out.cell_cases[ci] = (uint8_t)cs;
+            }
+        }
+    } else if (sm && lane == 0) {
+        atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
+    }
+    for (int t = 0; t < nt; ++t) {
+        const unsigned long long ti = tbase + t;
+        if (ti >= (unsigned long long)out.capacity_tris) break;
+        float pos[9];
+        unsigned long long key[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const int e = c_tab_e[cs][3 * t + v];
+            const int ax = e >> 2, u = e & 1, w = (e >> 1) & 1;
+            const int ox = ax == 0 ? 0 : u, oy = ax == 1 ? 0 : (ax == 0 ? u : w), oz = ax == 2 ? 0 : w;
+            const int blo = ox + 2 * oy + 4 * oz, bhi = blo + (1 << ax);
+            const float fa = fv[blo], fb = fv[bhi];
+            const float tt = fa / (fa - fb);
+            const int la = i + ox, lb = j + oy, lc = k + oz;
+            float px = fmaf((float)la, g.h, g.lo[0]);
+            float py = fmaf((float)lb, g.h, g.lo[1]);
+            float pz = fmaf((float)lc, g.h, g.lo[2]);
+            if (ax == 0) px = fmaf(tt, g.h, px);
+            else if (ax == 1) py = fmaf(tt, g.h, py);
+            else pz = fmaf(tt, g.h, pz);
+            pos[3 * v] = px;
+            pos[3 * v + 1] = py;
+            pos[3 * v + 2] = pz;
+            key[v] = (unsigned long long)ax * N13 + (unsigned long long)la +
+                     (unsigned long long)N1 * ((unsigned long long)lb + (unsigned long long)N1 * lc);
+        }
+        float *dst = out.tri_xyz + ti * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dst[q] = pos[q];
+        if (out.tri_keys) {
+            unsigned long long *kd = reinterpret_cast<unsigned long long *>(out.tri_keys) + ti * 3;
+            kd[0] = key[0];
+            kd[1] = key[1];
+            kd[2] = key[2];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    const unsigned long long M = s.ctr->marks;
+    const int N = g.N, N1 = N + 1;
+    const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long m0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); m0 < M;
          m0 += stride) {
         const unsigned long long m = m0 + lane;
         const bool valid = m < M;
         float fv[8];
-        int cs = 0, i = 0, j = 0, k = 0;
+        int i = 0, j = 0, k = 0;
         if (valid) {
             const unsigned long long r = s.marks_csr[m];
             const uint32_t col = mark_col(r);
@@ -462,76 +541,67 @@ __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
                 fv[q] = s.vval[idx];
                 fv[q + 4] = s.vval[idx + 1];
             }
-#pragma unroll
-            for (int b = 0; b < 8; ++b) cs |= (fv[b] < 0.f) << b;
         }
-        const bool surf = valid && cs != 0 && cs != 255;
-        const int nt = surf ? c_tab_n[cs] : 0;
-        // warp-exclusive prefix sum of the triangle counts, one atomic per warp
-        int x = nt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += y;
-        }
-        const int wtot = __shfl_sync(FULL, x, 31);
-        unsigned long long tbase = 0;
-        if (wtot) {
-            if (lane == 31) tbase = atomicAdd(&s.ctr->tris, (unsigned long long)wtot);
-            tbase = __shfl_sync(FULL, tbase, 31);
-        }
-        tbase += (unsigned long long)(x - nt);
-        const unsigned sm = __ballot_sync(FULL, surf);
-        if (sm && out.cell_ids) {
-            unsigned long long cbase = 0;
-            if (lane == 0) cbase = atomicAdd(&s.ctr->cells, (unsigned long long)__popc(sm));
-            cbase = __shfl_sync(FULL, cbase, 0);
-            if (surf) {
-                const unsigned long long ci = cbase + __popc(sm & lt);
-                if (ci < (unsigned long long)out.capacity_cells) {
-                    out.cell_ids[ci] = ((unsigned long long)i * N + j) * N + k;
-                    out.cell_cases[ci] = (uint8_t)cs;
-                }
-            }
-        } else if (sm && lane == 0) {
-            atomicAdd(&s.ctr->cells, (unsigned long long)__popc(sm));
-        }
-        for (int t = 0; t < nt; ++t) {
-            const unsigned long long ti = tbase + t;
-            if (ti >= (unsigned long long)out.capacity_tris) break;
-            float pos[9];
-            unsigned long long key[3];
-#pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                const int e = c_tab_e[cs][3 * t + v];
-                const int ax = e >> 2, u = e & 1, w = (e >> 1) & 1;
-                const int ox = ax == 0 ? 0 : u, oy = ax == 1 ? 0 : (ax == 0 ? u : w), oz = ax == 2 ? 0 : w;
-                const int blo = ox + 2 * oy + 4 * oz, bhi = blo + (1 << ax);
-                const float fa = fv[blo], fb = fv[bhi];
-                const float tt = fa / (fa - fb);
-                const int la = i + ox, lb = j + oy, lc = k + oz;
-                float px = fmaf((float)la, g.h, g.lo[0]);
-                float py = fmaf((float)lb, g.h, g.lo[1]);
-                float pz = fmaf((float)lc, g.h, g.lo[2]);
-                if (ax == 0) px = fmaf(tt, g.h, px);
-                else if (ax == 1) py = fmaf(tt, g.h, py);
-                else pz = fmaf(tt, g.h, pz);
-                pos[3 * v] = px;
-                pos[3 * v + 1] = py;
-                pos[3 * v + 2] = pz;
-                key[v] = (unsigned long long)ax * N13 + (unsigned long long)la +
-                         (unsigned long long)N1 * ((unsigned long long)lb + (unsigned long long)N1 * lc);
-            }
-            float *dst = out.tri_xyz + ti * 9;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) dst[q] = pos[q];
-            if (out.tri_keys) {
-                unsigned long long *kd = reinterpret_cast<unsigned long long *>(out.tri_keys) + ti * 3;
-                kd[0] = key[0];
-                kd[1] = key[1];
-                kd[2] = key[2];
-            }
-        }
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Enumeration (Sec. 2): f at every lattice point, Marching Cubes on every cell.
+// Lattice point (a,b,c) is stored at a + (N+1)(b + (N+1)c).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_lattice_csg(const Prim *__restrict__ gprims, int nprim, GridP g, Scratch s) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    const long long N1 = g.N + 1, n = N1 * N1 * N1;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const long long a = v % N1, b = (v / N1) % N1, c = v / (N1 * N1);
+        const float f = csg_eval(sprim, nprim, fmaf((float)a, g.h, g.lo[0]), fmaf((float)b, g.h, g.lo[1]),
+                                 fmaf((float)c, g.h, g.lo[2]));
+        if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+        s.lat[v] = f;
+    }
+}
+
+void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, cudaStream_t st) {
+    const size_t smem = (size_t)nprim * sizeof(Prim);
+    k_lattice_csg<<<4096, 256, smem, st>>>(prims, nprim, g, s);
+}
+
+__global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh out) {
+    const long long N = g.N, N1 = N + 1, n = N * N * N;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long m0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); m0 < n; m0 += stride) {
+        const long long m = m0 + lane;
+        const bool valid = m < n;
+        float fv[8];
+        int i = 0, j = 0, k = 0;
+        if (valid) {
+            k = (int)(m % N);
+            j = (int)((m / N) % N);
+            i = (int)(m / (N * N));
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const long long a = i + (b & 1), bb = j + ((b >> 1) & 1), c = k + ((b >> 2) & 1);
+                fv[b] = s.lat[a + N1 * (bb + N1 * c)];
+            }
+        }
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv);
+    }
+}
+
+__global__ void k_enum_stats(GridP g, Counters *c) {
+    const unsigned long long N = g.N, N1 = N + 1;
+    c->hop_evals = N1 * N1 * N1;  // evaluations of the enumeration
+    c->marks = N * N * N;         // every cell is polygonized
+    c->verts = N1 * N1 * N1;
+}
+
+void launch_enum_stats(const GridP &g, Scratch &s, cudaStream_t st) { k_enum_stats<<<1, 1, 0, st>>>(g, s.ctr); }
+
+void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st) {
+    k_mc_dense<<<nsm * 16, 256, 0, st>>>(g, s, out);
 }
 
 void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st) {

@@ -20,6 +20,8 @@ GH_SDB_CSG, GH_SDB_MLP = 0, 1
 GH_FP32, GH_BF16_REFINE = 0, 1
 GH_TAU_DIAGONAL, GH_TAU_HALF_DIAGONAL = 0, 1
 PRECISIONS = {"fp32": GH_FP32, "bf16": GH_BF16_REFINE, "bf16_refine": GH_BF16_REFINE}
+GH_METHOD_HOP, GH_METHOD_ENUM = 0, 1
+METHODS = {"hop": GH_METHOD_HOP, "enum": GH_METHOD_ENUM}
 
 _lock = threading.Lock()
 _lib = None
@@ -42,7 +44,8 @@ class SdbDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tau_mode", ctypes.c_int32), ("eps", ctypes.c_float),
-                ("sync", ctypes.c_int32), ("ray_block", ctypes.c_int32), ("mlp_tiles", ctypes.c_int32)]
+                ("sync", ctypes.c_int32), ("ray_block", ctypes.c_int32), ("mlp_tiles", ctypes.c_int32),
+                ("method", ctypes.c_int32)]
 
 
 STAT_FIELDS = ["status", "columns", "hop_evals", "marked_cells", "unique_vertices", "refined_vertices",
@@ -278,7 +281,8 @@ class Buffers:
         return {n: int(v[i]) for i, n in enumerate(STAT_FIELDS)}
 
 
-def options(precision="fp32", tau_mode=GH_TAU_DIAGONAL, eps=None, sync=True, ray_block=0, mlp_tiles=0) -> Options:
+def options(precision="fp32", tau_mode=GH_TAU_DIAGONAL, eps=None, sync=True, ray_block=0, mlp_tiles=0,
+            method="hop") -> Options:
     o = Options()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.tau_mode = int(tau_mode)
@@ -286,15 +290,16 @@ def options(precision="fp32", tau_mode=GH_TAU_DIAGONAL, eps=None, sync=True, ray
     o.sync = 1 if sync else 0
     o.ray_block = int(ray_block)
     o.mlp_tiles = int(mlp_tiles)
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
     return o
 
 
 def polygonize_into(sdb: Sdb, N, bufs: Buffers, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_DIAGONAL,
-                    eps=None, sync=True, stream=None, ray_block=0, mlp_tiles=0) -> int:
+                    eps=None, sync=True, stream=None, ray_block=0, mlp_tiles=0, method="hop") -> int:
     """Runs gh_polygonize into preallocated buffers; returns the status code
     (GH_ERR_CAPACITY is returned, not raised)."""
     g = _grid(N, lo, hi)
-    o = options(precision, tau_mode, eps, sync, ray_block, mlp_tiles)
+    o = options(precision, tau_mode, eps, sync, ray_block, mlp_tiles, method)
     rc = lib().gh_polygonize(ctypes.byref(g), sdb.handle, ctypes.byref(o), ctypes.byref(bufs.desc),
                              _stream_ptr(stream))
     if rc not in (GH_OK, GH_ERR_CAPACITY):
@@ -303,14 +308,14 @@ def polygonize_into(sdb: Sdb, N, bufs: Buffers, lo=-1.0, hi=1.0, precision="fp32
 
 
 def polygonize(sdb: Sdb, N, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_DIAGONAL, keys=False, cells=False,
-               eps=None, stream=None) -> Mesh:
+               eps=None, stream=None, method="hop") -> Mesh:
     """gh_polygonize with buffers sized (and re-sized) automatically; returns
     device tensors trimmed to the produced counts."""
     key = (int(N), bool(keys), bool(cells))
     cap = sdb._cap.get(key, 4 * int(N) * int(N) + 4096)
     for _ in range(3):
         bufs = Buffers(cap, keys=keys, cap_cells=cap if cells else 0)
-        rc = polygonize_into(sdb, N, bufs, lo, hi, precision, tau_mode, eps, True, stream)
+        rc = polygonize_into(sdb, N, bufs, lo, hi, precision, tau_mode, eps, True, stream, method=method)
         counts = bufs.counts.cpu().numpy()
         if rc == GH_OK:
             sdb._cap[key] = cap

@@ -53,3 +53,17 @@ def test_mlp_c2_fp32_sampled_n1024():
     assert st["cells"] > 40
     s = m.stats
     assert s["surface_cells"] > 1_000_000
+
+
+def test_enumeration_equals_hopping_mlp():
+    import meshutil
+    sdb, o = _pair(4, 64)
+    N = 48
+    e = gh.polygonize(sdb, N, keys=True, cells=True, method="enum")
+    hp = gh.polygonize(sdb, N, keys=True, cells=True)
+    ke, pe = meshutil.vertex_table(e.tri_keys.cpu().numpy(), e.tri_xyz.cpu().numpy())
+    kh, ph = meshutil.vertex_table(hp.tri_keys.cpu().numpy(), hp.tri_xyz.cpu().numpy())
+    assert (ke == kh).all() and np.array_equal(pe, ph)
+    parity.compare(e, o, N, ref=oracle.enum(o, N))
+    with pytest.raises(gh.GhError):
+        gh.polygonize(sdb, N, method="enum", precision="bf16", eps=1e-5)
