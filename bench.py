@@ -96,14 +96,18 @@ def run_reference(args):
         return
     # each step is a bounded sample so that --steps K --warmup W ends in minutes
     per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps)))
-    vals = []
+    for k in range(args.warmup):
+        oracle_sample(1.0, seed=900 + k)
+    vals, secs = [], []
     for k in range(args.steps):
         v, cores, sample, dt = oracle_sample(per_step, seed=123 + k)
         vals.append(v)
+        secs.append(dt)
     value = float(np.median(vals))
     line = {
         "impl": "reference", "metric": "surface cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
-        "steps": len(vals), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "steps": len(vals), "warmup": args.warmup, "ms_per_step": float(np.mean(secs)) * 1e3,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(WORKLOAD),
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -368,6 +368,11 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         const unsigned lt = (1u << lane) - 1u;
         int cur = 0;
         const Item *it = &items[0];
+        GridP g = it->g;  // the current item's grid and scratch, kept in registers
+        Counters *ctr = it->s.ctr;
+        unsigned long long *marks_raw = it->s.marks_raw;
+        uint32_t *colcount = it->s.colcount;
+        unsigned long long cap_marks = (unsigned long long)it->s.cap_marks;
         uint32_t col = NONE, rank = 0;
         int k = 0;
         bool done = false;
@@ -377,34 +382,52 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         float4 *w0b = sm.w0b[t];
         float *bmid = sm.bmid[t];
         float *wout = sm.wout[t];
+        // hopping: every warp claims columns 32 at a time and asks for its next
+        // range one claim ahead, so the atomic's round trip overlaps a whole
+        // step; the range base is kept in lane 0 until it is needed.
+        constexpr unsigned long long CLAIM = 32;
+        unsigned long long cur_lo = 0, cur_hi = 0, nxt = 0;
+        if (MODE == MODE_HOP && lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
+        // a mark found in the previous step, written once its slot is known
+        bool pend_mark = false;
+        unsigned long long pend_base = 0, pend_rec = 0;
+        unsigned pend_mask = 0;
         for (;;) {
             // 1. the work of this row, from item cur
-            const GridP &g = it->g;
             const int N = g.N;
             bool live = false;
             float px = 0.f, py = 0.f, pz = 0.f;
             if (MODE == MODE_HOP) {
-                const uint32_t ncols = (uint32_t)N * (uint32_t)N;
-                const bool need = col == NONE && !done;
-                const unsigned needm = __ballot_sync(FULL, need);
-                if (needm) {
-                    const int leader = __ffs(needm) - 1;
-                    unsigned long long base = 0;
-                    if (lane == leader) base = atomicAdd(&it->s.ctr->next_col, (unsigned long long)__popc(needm));
-                    base = __shfl_sync(FULL, base, leader);
-                    if (need) {
-                        const unsigned long long c = base + __popc(needm & lt);
-                        if (c < ncols) {
-                            col = (uint32_t)c;
-                            k = 0;
-                            rank = 0;
-                            const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
-                            x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
-                            y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
-                        } else {
-                            done = true;
+                const unsigned long long ncols = (unsigned long long)N * (unsigned long long)N;
+                unsigned needm = __ballot_sync(FULL, col == NONE && !done);
+                while (needm) {
+                    const unsigned long long hi = cur_hi < ncols ? cur_hi : ncols;
+                    const unsigned long long avail = hi > cur_lo ? hi - cur_lo : 0ull;
+                    if (avail == 0) {
+                        const unsigned long long nb = __shfl_sync(FULL, nxt, 0);
+                        if (nb >= ncols) {  // the item's queue is empty
+                            if (needm & (1u << lane)) done = true;
+                            break;
                         }
+                        cur_lo = nb;
+                        cur_hi = nb + CLAIM;
+                        if (lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
+                        continue;
                     }
+                    const unsigned take = (unsigned)(avail < 32ull ? avail : 32ull);
+                    // the first `take` needing lanes get cur_lo + rank
+                    const unsigned r = __popc(needm & lt);
+                    if ((needm & (1u << lane)) && r < take) {
+                        col = (uint32_t)(cur_lo + r);
+                        k = 0;
+                        rank = 0;
+                        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                        x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                        y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                    }
+                    const unsigned got = __popc(needm) < take ? __popc(needm) : take;
+                    cur_lo += got;
+                    needm = __ballot_sync(FULL, col == NONE && !done);
                 }
                 live = col != NONE;
                 if (live) {
@@ -415,9 +438,9 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             } else {
                 unsigned long long total = (unsigned long long)npts;
                 if (MODE == MODE_VERTS)
-                    total = (it->s.ctr->flags & STOP_FLAGS) ? 0ull : it->s.ctr->verts;
+                    total = (ctr->flags & STOP_FLAGS) ? 0ull : ctr->verts;
                 unsigned long long base = 0;
-                if (lane == 0) base = done ? total : atomicAdd(&it->s.ctr->next_tile, 32ull);
+                if (lane == 0) base = done ? total : atomicAdd(&ctr->next_tile, 32ull);
                 base = __shfl_sync(FULL, base, 0);
                 idx = base + lane;
                 live = idx < total;
@@ -453,8 +476,18 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             if (!any) {
                 // item cur has no work left for this tile: next item, or done
                 if (MODE == MODE_HOP) {
+                    if (pend_mark) {
+                        const unsigned long long b0 = __shfl_sync(FULL, pend_base, __ffs(pend_mask) - 1);
+                        if (pend_mask & (1u << lane)) {
+                            const unsigned long long mi = b0 + __popc(pend_mask & lt);
+                            if (mi < cap_marks) marks_raw[mi] = pend_rec;
+                            else atomicOr(&ctr->flags, FLAG_MARK_OVERFLOW);
+                        }
+                    }
+                    pend_mark = false;
+                    pend_mask = 0;
                     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
-                    if (lane == 0 && evals) atomicAdd(&it->s.ctr->hop_evals, evals);
+                    if (lane == 0 && evals) atomicAdd(&ctr->hop_evals, evals);
                     evals = 0;
                 }
                 ++cur;
@@ -468,8 +501,15 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     break;
                 }
                 it = &items[cur];
+                g = it->g;
+                ctr = it->s.ctr;
+                marks_raw = it->s.marks_raw;
+                colcount = it->s.colcount;
+                cap_marks = (unsigned long long)it->s.cap_marks;
                 col = NONE;
                 done = false;
+                cur_lo = cur_hi = 0;
+                if (MODE == MODE_HOP && lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
                 {
                     const MlpDev &mm = it->m;
                     for (int o = row; o < W; o += 128) {
@@ -502,6 +542,17 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             }
             fence_async_smem();
             mbar_arrive(&sm.a_full[t]);
+            if (MODE == MODE_HOP && pend_mark) {
+                // the previous step's marks: their slots came back during layer 0
+                const unsigned long long b0 = __shfl_sync(FULL, pend_base, __ffs(pend_mask) - 1);
+                if (pend_mask & (1u << lane)) {
+                    const unsigned long long mi = b0 + __popc(pend_mask & lt);
+                    if (mi < cap_marks) marks_raw[mi] = pend_rec;
+                    else atomicOr(&ctr->flags, FLAG_MARK_OVERFLOW);
+                }
+                pend_mark = false;
+                pend_mask = 0;
+            }
             // 3. hidden layers
             float gsum = 0.f;
             for (int l = 0; l < n_mid; ++l) {
@@ -565,13 +616,12 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             // 4. f, then the hop step or the store
             const float f = outer_f(m, px, py, pz, gsum + m.bout);
             if (MODE == MODE_HOP) {
-                const Scratch &s = it->s;
                 bool mark = false;
                 int step = 1;
                 if (live) {
                     float d = fabsf(f) - g.eps;
                     if (!isfinite(f)) {
-                        atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                        atomicOr(&ctr->flags, FLAG_NONFINITE);
                         d = 0.f;
                     }
                     if (d <= g.tau) {
@@ -583,17 +633,12 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 }
                 const unsigned mm = __ballot_sync(FULL, mark);
                 if (mm) {
+                    // claim the slots now; the records are written after the next layer 0
                     const int leader = __ffs(mm) - 1;
-                    unsigned long long base = 0;
-                    if (lane == leader) base = atomicAdd(&s.ctr->marks, (unsigned long long)__popc(mm));
-                    base = __shfl_sync(FULL, base, leader);
-                    if (mark) {
-                        const unsigned long long mi = base + __popc(mm & lt);
-                        if (mi < (unsigned long long)s.cap_marks)
-                            s.marks_raw[mi] = pack_mark(col, (uint32_t)k, rank);
-                        else
-                            atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
-                    }
+                    if (lane == leader) pend_base = atomicAdd(&ctr->marks, (unsigned long long)__popc(mm));
+                    pend_mark = true;
+                    pend_mask = mm;
+                    if (mark) pend_rec = pack_mark(col, (uint32_t)k, rank);
                 }
                 if (live) {
                     if (mark) {
@@ -603,7 +648,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                         k += step;
                     }
                     if (k >= N) {
-                        s.colcount[col] = rank;
+                        colcount[col] = rank;
                         col = NONE;
                     }
                 }
