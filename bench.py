@@ -261,6 +261,7 @@ def run_ours(args):
         "ms_per_mesh": ms, "surface_cells": cells, "triangles": st["triangles"], "hop_evals": st["hop_evals"],
         "marked_cells": st["marked_cells"], "unique_vertices": st["unique_vertices"],
         "refined_vertices": st["refined_vertices"],
+        "hop_row_utilization": st["hop_evals"] / st["row_slots"] if st.get("row_slots") else None,
         "phases_ms": phase_ms,
         "roofline": roof, "kernels": kern, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }

@@ -141,7 +141,10 @@ typedef struct {
     int64_t refined_vertices;/* of those, re-evaluated in FP32 (BF16 path)    */
     int64_t surface_cells;   /* marked cells with 0 < case < 255              */
     int64_t triangles;       /* triangles produced (may exceed capacity)      */
-    int64_t reserved[8];
+    int64_t row_slots;       /* neural hopper: rows run, live or idle (a tile */
+                             /* of 128 rows per step); hop_evals / row_slots  */
+                             /* is the share of the GEMM rows doing work      */
+    int64_t reserved[7];
 } gh_stats;
 
 /* Output description; every buffer is caller-owned device memory.

@@ -20,7 +20,8 @@ struct Counters {
     unsigned long long flags;      // error bits (FLAG_*)
     unsigned long long next_tile;  // work counter of point-list kernels
     unsigned long long next_tile2; // second work counter (refinement pass)
-    unsigned long long pad[6];
+    unsigned long long row_slots;  // rows the neural hopper ran (live or not): 128 per tile-step
+    unsigned long long pad[5];
 };
 
 enum : unsigned long long {

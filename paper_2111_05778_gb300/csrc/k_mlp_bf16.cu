@@ -382,12 +382,6 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         float4 *w0b = sm.w0b[t];
         float *bmid = sm.bmid[t];
         float *wout = sm.wout[t];
-        // hopping: every warp claims columns 32 at a time and asks for its next
-        // range one claim ahead, so the atomic's round trip overlaps a whole
-        // step; the range base is kept in lane 0 until it is needed.
-        constexpr unsigned long long CLAIM = 32;
-        unsigned long long cur_lo = 0, cur_hi = 0, nxt = 0;
-        if (MODE == MODE_HOP && lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
         // a mark found in the previous step, written once its slot is known
         bool pend_mark = false;
         unsigned long long pend_base = 0, pend_rec = 0;
@@ -398,36 +392,27 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             bool live = false;
             float px = 0.f, py = 0.f, pz = 0.f;
             if (MODE == MODE_HOP) {
-                const unsigned long long ncols = (unsigned long long)N * (unsigned long long)N;
-                unsigned needm = __ballot_sync(FULL, col == NONE && !done);
-                while (needm) {
-                    const unsigned long long hi = cur_hi < ncols ? cur_hi : ncols;
-                    const unsigned long long avail = hi > cur_lo ? hi - cur_lo : 0ull;
-                    if (avail == 0) {
-                        const unsigned long long nb = __shfl_sync(FULL, nxt, 0);
-                        if (nb >= ncols) {  // the item's queue is empty
-                            if (needm & (1u << lane)) done = true;
-                            break;
+                const uint32_t ncols = (uint32_t)N * (uint32_t)N;
+                const bool need = col == NONE && !done;
+                const unsigned needm = __ballot_sync(FULL, need);
+                if (needm) {
+                    const int leader = __ffs(needm) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader) base = atomicAdd(&ctr->next_col, (unsigned long long)__popc(needm));
+                    base = __shfl_sync(FULL, base, leader);
+                    if (need) {
+                        const unsigned long long c = base + __popc(needm & lt);
+                        if (c < ncols) {
+                            col = (uint32_t)c;
+                            k = 0;
+                            rank = 0;
+                            const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+                            x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
+                            y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
+                        } else {
+                            done = true;
                         }
-                        cur_lo = nb;
-                        cur_hi = nb + CLAIM;
-                        if (lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
-                        continue;
                     }
-                    const unsigned take = (unsigned)(avail < 32ull ? avail : 32ull);
-                    // the first `take` needing lanes get cur_lo + rank
-                    const unsigned r = __popc(needm & lt);
-                    if ((needm & (1u << lane)) && r < take) {
-                        col = (uint32_t)(cur_lo + r);
-                        k = 0;
-                        rank = 0;
-                        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
-                        x = fmaf((float)i + 0.5f, g.h, g.lo[0]);
-                        y = fmaf((float)j + 0.5f, g.h, g.lo[1]);
-                    }
-                    const unsigned got = __popc(needm) < take ? __popc(needm) : take;
-                    cur_lo += got;
-                    needm = __ballot_sync(FULL, col == NONE && !done);
                 }
                 live = col != NONE;
                 if (live) {
@@ -508,8 +493,6 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 cap_marks = (unsigned long long)it->s.cap_marks;
                 col = NONE;
                 done = false;
-                cur_lo = cur_hi = 0;
-                if (MODE == MODE_HOP && lane == 0) nxt = atomicAdd(&ctr->next_col, CLAIM);
                 {
                     const MlpDev &mm = it->m;
                     for (int o = row; o < W; o += 128) {
@@ -524,6 +507,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             if (row == 0) {
                 sm.cur_wbf[t] = it->m.wbf;
                 mbar_arrive(&sm.item_ready[t]);
+                if (MODE == MODE_HOP) atomicAdd(&ctr->row_slots, 128ull);
             }
             const MlpDev &m = it->m;
             // 2. layer 0 (FP32) -> A operand

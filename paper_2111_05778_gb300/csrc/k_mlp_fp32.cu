@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
             ++cur;
             continue;
         }
+        if (tid == 0) atomicAdd(&s.ctr->row_slots, (unsigned long long)TM);
         mlp_tile<W>(it.m, sm);
         if (tid < TM) {
             bool mark = false;

@@ -765,6 +765,7 @@ __global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
         st->refined_vertices = (long long)c.refine;
         st->surface_cells = (long long)c.cells;
         st->triangles = (long long)c.tris;
+        st->row_slots = (long long)c.row_slots;
     }
 }
 

@@ -49,11 +49,11 @@ class Options(ctypes.Structure):
 
 
 STAT_FIELDS = ["status", "columns", "hop_evals", "marked_cells", "unique_vertices", "refined_vertices",
-               "surface_cells", "triangles"]
+               "surface_cells", "triangles", "row_slots"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 8)]
+    _fields_ = [(n, ctypes.c_int64) for n in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 7)]
 
 
 class MeshDesc(ctypes.Structure):
