@@ -61,6 +61,15 @@ extern "C" {
 #define GH_PRIM_SPHERE 0 /* param[0] = radius                                 */
 #define GH_PRIM_TORUS 1  /* around local y: param[0] = major R, param[1] = r   */
 #define GH_PRIM_BOX 2    /* exact box distance (Sec. 4.2), half sizes param[] */
+/* 3..6 with the sphere, box and torus are the seven basic primitives of the
+ * first test scene (Sec. 5.1); each is an exact distance, param[2] unused.
+ * gh_backward differentiates all seven (centre and param[0..1]). */
+#define GH_PRIM_CAPSULE 3  /* segment (0,-H,0)-(0,H,0) widened by r: param = H, r  */
+#define GH_PRIM_CYLINDER 4 /* capped, around local y: param = radius r, half height H */
+#define GH_PRIM_HEXPRISM 5 /* regular hexagon of apothem a in the local xz-plane   */
+                           /* (edges facing 0, 60, ... degrees), |y| <= H: a, H   */
+#define GH_PRIM_CONE 6     /* solid cone: base disc radius R at y = -H, apex at +H; */
+                           /* R > 0 and H > 0 (else GH_ERR_ARG)                  */
 #define GH_OP_UNION 0
 #define GH_OP_SUBTRACT 1
 #define GH_OP_INTERSECT 2

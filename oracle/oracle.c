@@ -49,7 +49,7 @@
 /* SDB descriptions                                                          */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_SPHERE = 0, OR_TORUS = 1, OR_BOX = 2 };
+enum { OR_SPHERE = 0, OR_TORUS = 1, OR_BOX = 2, OR_CAPSULE = 3, OR_CYLINDER = 4, OR_HEXPRISM = 5, OR_CONE = 6 };
 enum { OR_UNION = 0, OR_SUBTRACT = 1, OR_INTERSECT = 2 };
 #define OR_PRIM_STRIDE 17 /* type, op, c[3], p[3], rot[9] */
 
@@ -93,6 +93,66 @@ static double d_box(const double *q, const double *prm) {
     return sqrt(out2) + (inmax < 0 ? inmax : 0.0);
 }
 
+/* Capsule: the points within r of the segment from (0,-H,0) to (0,H,0). */
+static double d_capsule(const double *q, const double *prm) {
+    double y = q[1] < -prm[0] ? -prm[0] : (q[1] > prm[0] ? prm[0] : q[1]);
+    double v[3] = {q[0], q[1] - y, q[2]};
+    return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - prm[1];
+}
+
+/* Capped cylinder around the local y axis: radius r, half height H.  In the
+ * (radius, height) half-plane the solid is the rectangle [0,r] x [-H,H]. */
+static double d_cylinder(const double *q, const double *prm) {
+    double e0 = sqrt(q[0] * q[0] + q[2] * q[2]) - prm[0], e1 = fabs(q[1]) - prm[1];
+    double o0 = e0 > 0 ? e0 : 0.0, o1 = e1 > 0 ? e1 : 0.0;
+    double in = e0 > e1 ? e0 : e1;
+    return sqrt(o0 * o0 + o1 * o1) + (in < 0 ? in : 0.0);
+}
+
+/* 2-D signed distance to the regular hexagon of apothem a whose edges face
+ * the directions 0, 60, ..., 300 degrees: by symmetry fold into the wedge of
+ * angles [-30, 30] degrees, where the nearest edge is x = a, |z| <= a/sqrt(3). */
+static double d_hexagon2(double x, double z, double a) {
+    x = fabs(x);
+    z = fabs(z);
+    const double mx = -0.5, mz = sqrt(3.0) / 2; /* normal of the 30-degree mirror */
+    double dot = x * mx + z * mz;
+    if (dot > 0) {
+        x -= 2 * dot * mx;
+        z -= 2 * dot * mz;
+    }
+    double lim = a / sqrt(3.0), zc = z < -lim ? -lim : (z > lim ? lim : z);
+    double v0 = x - a, v1 = z - zc, n = sqrt(v0 * v0 + v1 * v1);
+    return v0 < 0 ? -n : n;
+}
+
+/* Hexagonal prism: the hexagon (apothem a) in the local xz-plane, extruded
+ * over |y| <= H. */
+static double d_hexprism(const double *q, const double *prm) {
+    double e0 = d_hexagon2(q[0], q[2], prm[0]), e1 = fabs(q[1]) - prm[1];
+    double o0 = e0 > 0 ? e0 : 0.0, o1 = e1 > 0 ? e1 : 0.0;
+    double in = e0 > e1 ? e0 : e1;
+    return sqrt(o0 * o0 + o1 * o1) + (in < 0 ? in : 0.0);
+}
+
+/* Solid cone around the local y axis: base disc of radius R at y = -H, apex at
+ * y = +H.  In the (radius rho, height y) half-plane the solid is the triangle
+ * (0,-H), (R,-H), (0,H); its boundary there is the base segment and the slant
+ * segment (the axis is inside the solid of revolution). */
+static double d_cone(const double *q, const double *prm) {
+    double R = prm[0], H = prm[1];
+    double rho = sqrt(q[0] * q[0] + q[2] * q[2]), y = q[1];
+    double bs = rho < 0 ? 0 : (rho > R ? R : rho);
+    double b0 = rho - bs, b1 = y + H, db = sqrt(b0 * b0 + b1 * b1);
+    double e0 = -R, e1 = 2 * H;
+    double t = ((rho - R) * e0 + (y + H) * e1) / (e0 * e0 + e1 * e1);
+    t = t < 0 ? 0 : (t > 1 ? 1 : t);
+    double s0 = rho - (R + t * e0), s1 = y - (-H + t * e1), ds = sqrt(s0 * s0 + s1 * s1);
+    double d = db < ds ? db : ds;
+    int inside = y > -H && y < H && rho * 2 * H < R * (H - y);
+    return inside ? -d : d;
+}
+
 static double prim_eval(const double *pr, const double *p) {
     const double *c = pr + 2, *prm = pr + 5, *R = pr + 8;
     double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
@@ -101,6 +161,10 @@ static double prim_eval(const double *pr, const double *p) {
     switch ((int)pr[0]) {
     case OR_SPHERE: return d_sphere(q, prm);
     case OR_TORUS: return d_torus(q, prm);
+    case OR_CAPSULE: return d_capsule(q, prm);
+    case OR_CYLINDER: return d_cylinder(q, prm);
+    case OR_HEXPRISM: return d_hexprism(q, prm);
+    case OR_CONE: return d_cone(q, prm);
     default: return d_box(q, prm);
     }
 }
@@ -840,6 +904,35 @@ static double prim_grad(const double *pr, const double *p, double *gp /*dd/dp*/,
         }
         gs[1] = -1.0;
         break;
+    }
+    case OR_CAPSULE:
+    case OR_CYLINDER:
+    case OR_HEXPRISM:
+    case OR_CONE: {
+        /* derivatives of these piecewise-smooth distances by central
+         * differences of the closed forms above (step 1e-7 of the unit
+         * domain; FP64 keeps them to about 1e-9) */
+        double pp[17], hh = 1e-7;
+        for (int i = 0; i < 17; ++i) pp[i] = pr[i];
+        val = prim_eval(pr, p);
+        for (int a = 0; a < 3; ++a) {
+            double hi_[3] = {p[0], p[1], p[2]}, lo_[3] = {p[0], p[1], p[2]};
+            hi_[a] += hh;
+            lo_[a] -= hh;
+            gq[a] = 0.0;
+            gs[a] = 0.0;
+            double dh = prim_eval(pr, hi_), dl = prim_eval(pr, lo_);
+            gp[a] = (dh - dl) / (2 * hh);
+        }
+        for (int a = 0; a < 2; ++a) {
+            pp[5 + a] = pr[5 + a] + hh;
+            double dh = prim_eval(pp, p);
+            pp[5 + a] = pr[5 + a] - hh;
+            double dl = prim_eval(pp, p);
+            pp[5 + a] = pr[5 + a];
+            gs[a] = (dh - dl) / (2 * hh);
+        }
+        return val;
     }
     default: {
         double e[3], o2 = 0.0;

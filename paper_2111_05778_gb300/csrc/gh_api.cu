@@ -255,12 +255,14 @@ static int create_csg(gh_sdb *s, const gh_sdb_desc *d) {
     memcpy(pr.data(), (const char *)d->blob + sizeof(h), pr.size() * sizeof(gh_csg_prim));
     for (int i = 0; i < h.n_prim; ++i) {
         const gh_csg_prim &p = pr[i];
-        if (p.type < 0 || p.type > 2) return fail(GH_ERR_ARG, "primitive %d: unknown type %d", i, p.type);
+        if (p.type < 0 || p.type > GH_PRIM_CONE) return fail(GH_ERR_ARG, "primitive %d: unknown type %d", i, p.type);
         if (p.op < 0 || p.op > 2) return fail(GH_ERR_ARG, "primitive %d: unknown op %d", i, p.op);
         for (int q = 0; q < 3; ++q)
             if (!isfinite(p.centre[q]) || !isfinite(p.param[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite", i);
         for (int q = 0; q < 9; ++q)
             if (!isfinite(p.rot[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite rotation", i);
+        if (p.type == GH_PRIM_CONE && !(p.param[0] > 0.f && p.param[1] > 0.f))
+            return fail(GH_ERR_ARG, "primitive %d: cone needs R > 0 and H > 0", i);
         // the shrink factor lambda of Sec. 5.2 applies to analytic SDBs as a
         // scale of the distances: fold it into the primitives' parameters is
         // not possible for min/max of differently scaled terms, so lambda is

@@ -249,6 +249,13 @@ void adjoint_fill_ones(float *p, long long n, cudaStream_t st) { k_fill<<<256, 2
 //           dd/dq = (a qx/|(qx,qz)|, qy, a qz/|(qx,qz)|) / |(a,qy)|, dd/dR = -a/|(a,qy)|, dd/dr = -1
 //   box     e = |q| - h; outside: d = |max(e,0)|, dd/dq = sign(q) max(e,0)/d, dd/dh = -max(e,0)/d;
 //           inside: d = max_k e_k, dd/dq_k = sign(q_k), dd/dh_k = -1 (largest k)
+//   capsule d = |q - (0, clamp(qy,-H,H), 0)| - r; the clamp moves with H past the caps
+//   cylinder, hexagonal prism: the box rule in 2-D on (e0, |qy| - H), e0 the
+//           radial (resp. folded hexagon) distance, differentiated through the
+//           fold's mirror
+//   cone    distance to the nearer of the base segment and the slant segment in
+//           (rho, qy); the closest point's derivative in R and H is that of its
+//           segment's parametrisation (base: (min(rho,R), -H); slant: (R - tR, 2tH - H))
 // dd/dv = Rot^T dd/dq and dd/dc = -dd/dv.  Each vertex contributes
 // s_v df/dtheta_a to its primitive a only.
 // ---------------------------------------------------------------------------
@@ -281,6 +288,113 @@ __device__ float csg_prim_grad(const Prim &P, float x, float y, float z, float *
             gs[0] = -a / n;
         }
         gs[1] = -1.f;
+    } else if (P.type == GH_PRIM_CAPSULE) {
+        // u = q - (0, clamp(qy, -H, H), 0), d = |u| - r
+        const float H = P.p[0];
+        const float yc = fminf(fmaxf(q1, -H), H), u1 = q1 - yc;
+        const float n = sqrtf(q0 * q0 + u1 * u1 + q2 * q2);
+        val = n - P.p[1];
+        if (n > 0.f) {
+            g0 = q0 / n;
+            g1 = u1 / n;
+            g2 = q2 / n;
+            gs[0] = q1 > H ? -u1 / n : (q1 < -H ? u1 / n : 0.f);
+        }
+        gs[1] = -1.f;
+    } else if (P.type == GH_PRIM_CYLINDER || P.type == GH_PRIM_HEXPRISM) {
+        // e0: radial (cylinder) or hexagon (prism) distance, e1 = |qy| - H
+        float e0, d0x = 0.f, d0z = 0.f, d0p = -1.f;
+        if (P.type == GH_PRIM_CYLINDER) {
+            const float rho = sqrtf(q0 * q0 + q2 * q2);
+            e0 = rho - P.p[0];
+            if (rho > 0.f) {
+                d0x = q0 / rho;
+                d0z = q2 / rho;
+            }
+        } else {
+            // folded hexagon: |x|, |z|, then the mirror at 30 degrees
+            const float a = P.p[0];
+            const float sx = q0 < 0.f ? -1.f : 1.f, sz = q2 < 0.f ? -1.f : 1.f;
+            float x = fabsf(q0), z = fabsf(q2);
+            const float mx = -0.5f, mz = 0.8660254037844386f;
+            const float dot = x * mx + z * mz;
+            const bool refl = dot > 0.f;
+            if (refl) {
+                x -= 2.f * dot * mx;
+                z -= 2.f * dot * mz;
+            }
+            const float lim = a * 0.5773502691896258f;
+            const float v0 = x - a, v1 = z - fminf(fmaxf(z, -lim), lim);
+            const float n = sqrtf(v0 * v0 + v1 * v1), sg = v0 < 0.f ? -1.f : 1.f;
+            e0 = sg * n;
+            float gx = 0.f, gz = 0.f;
+            if (n > 0.f) {
+                gx = sg * v0 / n;
+                gz = sg * v1 / n;
+                const float dv1 = z > lim ? -0.5773502691896258f : (z < -lim ? 0.5773502691896258f : 0.f);
+                d0p = sg * (-v0 + v1 * dv1) / n;
+            }
+            if (refl) {  // the mirror is its own transpose
+                const float gd = gx * mx + gz * mz;
+                gx -= 2.f * gd * mx;
+                gz -= 2.f * gd * mz;
+            }
+            d0x = sx * gx;
+            d0z = sz * gz;
+        }
+        const float e1 = fabsf(q1) - P.p[1];
+        float w0, w1;
+        if (e0 > 0.f || e1 > 0.f) {
+            const float o0 = fmaxf(e0, 0.f), o1 = fmaxf(e1, 0.f), n = sqrtf(o0 * o0 + o1 * o1);
+            val = n;
+            w0 = o0 / n;
+            w1 = o1 / n;
+        } else {
+            val = fmaxf(e0, e1);
+            w0 = e0 >= e1 ? 1.f : 0.f;
+            w1 = e0 >= e1 ? 0.f : 1.f;
+        }
+        g0 = w0 * d0x;
+        g2 = w0 * d0z;
+        g1 = w1 * (q1 < 0.f ? -1.f : 1.f);
+        gs[0] = w0 * d0p;
+        gs[1] = -w1;
+    } else if (P.type == GH_PRIM_CONE) {
+        const float R = P.p[0], H = P.p[1];
+        const float rho = sqrtf(q0 * q0 + q2 * q2), y = q1;
+        const float bs = fminf(fmaxf(rho, 0.f), R);
+        const float b0 = rho - bs, b1 = y + H, db = sqrtf(b0 * b0 + b1 * b1);
+        const float e0 = -R, e1 = 2.f * H;
+        float t = ((rho - R) * e0 + (y + H) * e1) / (e0 * e0 + e1 * e1);
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        const float s0 = rho - (R + t * e0), s1 = y - (-H + t * e1), ds = sqrtf(s0 * s0 + s1 * s1);
+        const bool inside = y > -H && y < H && rho * 2.f * H < R * (H - y);
+        const float sg = inside ? -1.f : 1.f;
+        float v0, v1, n, cR0, cH1;
+        if (db < ds) {
+            v0 = b0;
+            v1 = b1;
+            n = db;
+            cR0 = rho > R ? 1.f : 0.f;  // d(closest)/dR = (cR0, 0), d(closest)/dH = (0, cH1)
+            cH1 = -1.f;
+        } else {
+            v0 = s0;
+            v1 = s1;
+            n = ds;
+            cR0 = 1.f - t;
+            cH1 = 2.f * t - 1.f;
+        }
+        val = sg * n;
+        if (n > 0.f) {
+            const float gr = sg * v0 / n, gy = sg * v1 / n;
+            if (rho > 0.f) {
+                g0 = gr * q0 / rho;
+                g2 = gr * q2 / rho;
+            }
+            g1 = gy;
+            gs[0] = -sg * v0 * cR0 / n;
+            gs[1] = -sg * v1 * cH1 / n;
+        }
     } else {
         const float q[3] = {q0, q1, q2};
         float e[3], o2 = 0.f, g[3] = {0.f, 0.f, 0.f};

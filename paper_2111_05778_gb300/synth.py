@@ -15,10 +15,17 @@ Shapes (the paper's learned SDBs and scenes are not available, Sec. 5):
   each matrix divided by its largest singular value (so g and f are
   1-Lipschitz, i.e. signed distance bounds, Sec. 1) and N(0, 0.01^2) biases.
 * ``batch_items()``: 64 (kind, seed, N, width) items mixing both generators.
+* ``primitive_scene(seed)``: the seven basic primitives of the paper's first
+  scene (Sec. 5.1: sphere, cube, cone, cylinder, torus, hexagonal prism and
+  capsule), one of each, randomly rotated, in a union.
 
 Primitive rows are 17 float64 numbers:
 ``type, op, cx, cy, cz, p0, p1, p2, rot[9]`` with type 0 sphere (p0 = r),
-1 torus around the local y axis (p0 = R, p1 = r), 2 box (half sizes p0..p2);
+1 torus around the local y axis (p0 = R, p1 = r), 2 box (half sizes p0..p2),
+3 capsule (segment (0,-p0,0)-(0,p0,0), radius p1), 4 capped cylinder around
+the local y axis (radius p0, half height p1), 5 hexagonal prism (apothem p0 in
+the local xz-plane, half height p1), 6 cone (base radius p0 at y = -p1, apex
+at y = +p1);
 op 0 union, 1 subtract, 2 intersect, applied as a left fold; ``rot`` maps
 world offsets to the primitive's local frame (row-major).
 """
@@ -27,7 +34,7 @@ from __future__ import annotations
 import numpy as np
 
 PRIM_STRIDE = 17
-SPHERE, TORUS, BOX = 0, 1, 2
+SPHERE, TORUS, BOX, CAPSULE, CYLINDER, HEXPRISM, CONE = 0, 1, 2, 3, 4, 5, 6
 UNION, SUBTRACT, INTERSECT = 0, 1, 2
 
 MLP_R0, MLP_ALPHA, MLP_BETA = 0.6, 0.1, 1.1
@@ -101,6 +108,40 @@ def csg_prims(seed: int, n_sphere=24, n_torus=8, n_box=4) -> np.ndarray:
         c = rng.uniform(-0.7, 0.7, 3)
         hs = rng.uniform(0.05, 0.15, 3)
         rows.append(prim_row(BOX, SUBTRACT, c, hs))
+    return np.stack(rows)
+
+
+def primitive_scene(seed: int = 0) -> np.ndarray:
+    """One of each of the seven primitives, centres at the middle and on a
+    hexagon of radius 0.55 in the xy-plane (z U[-0.15,0.15]), each under a
+    rotation from a normalised 4-D Gaussian quaternion, sizes drawn in the
+    order sphere r U[0.18,0.25]; box half sizes U[0.12,0.2]; cone R
+    U[0.15,0.22], H U[0.15,0.22]; cylinder r U[0.1,0.18], H U[0.12,0.2];
+    torus R U[0.14,0.2], r U[0.04,0.07]; prism a U[0.1,0.18], H U[0.1,0.18];
+    capsule H U[0.08,0.15], r U[0.06,0.1]."""
+    rng = np.random.default_rng(seed)
+    ang = np.arange(6) * (np.pi / 3)
+    centres = [np.zeros(2)] + [0.55 * np.array([np.cos(a), np.sin(a)]) for a in ang]
+    kinds = [SPHERE, BOX, CONE, CYLINDER, TORUS, HEXPRISM, CAPSULE]
+    rows = []
+    for kind, cxy in zip(kinds, centres):
+        c = np.array([cxy[0], cxy[1], rng.uniform(-0.15, 0.15)])
+        rot = _quat_rot(rng.standard_normal(4))
+        if kind == SPHERE:
+            prm = [rng.uniform(0.18, 0.25)]
+        elif kind == BOX:
+            prm = rng.uniform(0.12, 0.2, 3)
+        elif kind == CONE:
+            prm = [rng.uniform(0.15, 0.22), rng.uniform(0.15, 0.22)]
+        elif kind == CYLINDER:
+            prm = [rng.uniform(0.1, 0.18), rng.uniform(0.12, 0.2)]
+        elif kind == TORUS:
+            prm = [rng.uniform(0.14, 0.2), rng.uniform(0.04, 0.07)]
+        elif kind == HEXPRISM:
+            prm = [rng.uniform(0.1, 0.18), rng.uniform(0.1, 0.18)]
+        else:
+            prm = [rng.uniform(0.08, 0.15), rng.uniform(0.06, 0.1)]
+        rows.append(prim_row(kind, UNION, c, prm, rot))
     return np.stack(rows)
 
 

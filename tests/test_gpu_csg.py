@@ -112,6 +112,10 @@ def test_invalid_arguments():
     bad[0, 0] = 7
     with pytest.raises(gh.GhError):
         gh.CsgSdb(bad)
+    flat = synth.prim_row(synth.CONE, synth.UNION, [0, 0, 0], [0.2, 0.0])[None]
+    with pytest.raises(gh.GhError) as e:
+        gh.CsgSdb(flat)
+    assert e.value.code == gh.GH_ERR_ARG
 
 
 def test_repeat_calls_are_identical():
@@ -152,3 +156,29 @@ def test_enumeration_equals_hopping_and_oracle(N):
             meshutil.canonical_tris(hp.tri_keys.cpu().numpy())).all()
     o = oracle.csg(prims)
     parity.compare(e, o, N, ref=oracle.enum(o, N))
+
+
+@pytest.mark.parametrize("N,lo,hi", [(141, -1.0, 1.0), (200, -0.8, 0.8)])
+def test_primitive_scene_matches_oracle(N, lo, hi):
+    """The seven primitives of the paper's first scene (Sec. 5.1), rotated, in
+    a union: every cell against the oracle's enumeration."""
+    prims = synth.primitive_scene(0)
+    m = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True, cells=True)
+    o = oracle.csg(prims)
+    ref = oracle.enum(o, N, lo, hi)
+    st = parity.compare(m, o, N, lo, hi, ref=ref)
+    assert st["cells"] > 5000
+
+
+def test_primitive_distances_match_oracle():
+    """Each new primitive alone, evaluated at points around it (edges, caps
+    and apex included), against the FP64 closed forms."""
+    rng = np.random.default_rng(4)
+    for kind in (synth.CAPSULE, synth.CYLINDER, synth.HEXPRISM, synth.CONE):
+        q = rng.standard_normal(4)
+        prims = synth.prim_row(kind, synth.UNION, rng.uniform(-0.2, 0.2, 3), rng.uniform(0.1, 0.3, 2),
+                               synth._quat_rot(q))[None]
+        P = rng.uniform(-0.6, 0.6, (20000, 3)).astype(np.float32)
+        got = gh.eval_points(gh.CsgSdb(prims), torch.tensor(P, device="cuda")).cpu().numpy().astype(np.float64)
+        ref = oracle.csg(prims).eval(P.astype(np.float64))
+        assert np.abs(got - ref).max() < parity.DELTA32, kind
