@@ -256,6 +256,9 @@ void adjoint_fill_ones(float *p, long long n, cudaStream_t st) { k_fill<<<256, 2
 //   cone    distance to the nearer of the base segment and the slant segment in
 //           (rho, qy); the closest point's derivative in R and H is that of its
 //           segment's parametrisation (base: (min(rho,R), -H); slant: (R - tR, 2tH - H))
+//   prism and cone take the outward normal of the nearest edge or segment as the
+//   direction wherever the closest point is inside it: at a mesh vertex p lies
+//   on the surface and p - closest is rounding noise
 // dd/dv = Rot^T dd/dq and dd/dc = -dd/dv.  Each vertex contributes
 // s_v df/dtheta_a to its primitive a only.
 // ---------------------------------------------------------------------------
@@ -327,11 +330,12 @@ __device__ float csg_prim_grad(const Prim &P, float x, float y, float z, float *
             const float v0 = x - a, v1 = z - fminf(fmaxf(z, -lim), lim);
             const float n = sqrtf(v0 * v0 + v1 * v1), sg = v0 < 0.f ? -1.f : 1.f;
             e0 = sg * n;
-            float gx = 0.f, gz = 0.f;
-            if (n > 0.f) {
+            float gx = 1.f, gz = 0.f;  // inside the edge's span: its outward normal
+            d0p = -1.f;
+            if (v1 != 0.f && n > 0.f) {  // past a corner: the corner's direction
                 gx = sg * v0 / n;
                 gz = sg * v1 / n;
-                const float dv1 = z > lim ? -0.5773502691896258f : (z < -lim ? 0.5773502691896258f : 0.f);
+                const float dv1 = z > lim ? -0.5773502691896258f : 0.5773502691896258f;
                 d0p = sg * (-v0 + v1 * dv1) / n;
             }
             if (refl) {  // the mirror is its own transpose
@@ -370,31 +374,40 @@ __device__ float csg_prim_grad(const Prim &P, float x, float y, float z, float *
         const float s0 = rho - (R + t * e0), s1 = y - (-H + t * e1), ds = sqrtf(s0 * s0 + s1 * s1);
         const bool inside = y > -H && y < H && rho * 2.f * H < R * (H - y);
         const float sg = inside ? -1.f : 1.f;
-        float v0, v1, n, cR0, cH1;
+        // gradient direction: the segment's outward normal where the closest
+        // point lies inside the segment (at a surface point p - closest is
+        // rounding noise), the direction from the closest end point otherwise
+        float nr, ny, cR0, cH1, n;
         if (db < ds) {
-            v0 = b0;
-            v1 = b1;
             n = db;
             cR0 = rho > R ? 1.f : 0.f;  // d(closest)/dR = (cR0, 0), d(closest)/dH = (0, cH1)
             cH1 = -1.f;
+            nr = 0.f;
+            ny = -1.f;
+            if (rho > R) {
+                nr = n > 0.f ? sg * b0 / n : 0.f;
+                ny = n > 0.f ? sg * b1 / n : 0.f;
+            }
         } else {
-            v0 = s0;
-            v1 = s1;
             n = ds;
             cR0 = 1.f - t;
             cH1 = 2.f * t - 1.f;
+            const float il = rsqrtf(e0 * e0 + e1 * e1);
+            nr = e1 * il;
+            ny = -e0 * il;
+            if (t <= 0.f || t >= 1.f) {
+                nr = n > 0.f ? sg * s0 / n : 0.f;
+                ny = n > 0.f ? sg * s1 / n : 0.f;
+            }
         }
         val = sg * n;
-        if (n > 0.f) {
-            const float gr = sg * v0 / n, gy = sg * v1 / n;
-            if (rho > 0.f) {
-                g0 = gr * q0 / rho;
-                g2 = gr * q2 / rho;
-            }
-            g1 = gy;
-            gs[0] = -sg * v0 * cR0 / n;
-            gs[1] = -sg * v1 * cH1 / n;
+        if (rho > 0.f) {
+            g0 = nr * q0 / rho;
+            g2 = nr * q2 / rho;
         }
+        g1 = ny;
+        gs[0] = -nr * cR0;
+        gs[1] = -ny * cH1;
     } else {
         const float q[3] = {q0, q1, q2};
         float e[3], o2 = 0.f, g[3] = {0.f, 0.f, 0.f};
