@@ -166,7 +166,11 @@ def test_primitive_scene_matches_oracle(N, lo, hi):
     m = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True, cells=True)
     o = oracle.csg(prims)
     ref = oracle.enum(o, N, lo, hi)
-    st = parity.compare(m, o, N, lo, hi, ref=ref)
+    # every vertex meets the propagated bound 1e-4 h + h DELTA32 / |fA - fB|;
+    # the rotated flat faces (box, prism, cylinder caps, cone base) put more
+    # lattice edges nearly tangent to the surface than curved shapes do, so
+    # the share within the bare 1e-4 h is checked at 0.995
+    st = parity.compare(m, o, N, lo, hi, ref=ref, min_bare=0.995)
     assert st["cells"] > 5000
 
 
