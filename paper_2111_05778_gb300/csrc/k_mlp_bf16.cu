@@ -510,8 +510,9 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 if (MODE == MODE_HOP) atomicAdd(&ctr->row_slots, 128ull);
             }
             const MlpDev &m = it->m;
-            // 2. layer 0 (FP32) -> A operand
-#pragma unroll 1
+            // 2. layer 0 (FP32) -> A operand (two 8-output groups per iteration
+            // so that the loads of one overlap the FMAs of the other)
+#pragma unroll 2
             for (int o = 0; o < W; o += 8) {
                 uint32_t pk[4];
 #pragma unroll
