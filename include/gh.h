@@ -153,7 +153,9 @@ typedef struct {
     int64_t row_slots;       /* neural hopper: rows run, live or idle (a tile */
                              /* of 128 rows per step); hop_evals / row_slots  */
                              /* is the share of the GEMM rows doing work      */
-    int64_t reserved[7];
+    int64_t mesh_vertices;   /* crossing lattice edges = vertices of the      */
+                             /* indexed mesh (when it is requested)           */
+    int64_t reserved[6];
 } gh_stats;
 
 /* Output description; every buffer is caller-owned device memory.
@@ -165,7 +167,19 @@ typedef struct {
  * cell_ids / cell_cases / capacity_cells / n_cells: optional (NULL) list of
  *            the surface cells (0 < case < 255) with their case index,
  *            same capacity protocol.
- * stats:     optional device gh_stats. */
+ * stats:     optional device gh_stats.
+ * Indexed mesh (optional; no counterpart in the paper, which outputs the
+ * triangles of Marching Cubes): one vertex per crossing lattice edge,
+ * numbered in the order of its lower end point in the pipeline's lattice-
+ * vertex list (x, y, z edges in that order), so the numbering does not depend
+ * on the triangle order.
+ * vert_xyz:  [capacity_verts][3] float32 vertex positions, bit-identical to
+ *            the soup's positions of the same edge, or NULL.
+ * tri_idx:   [capacity_tris][3] int32 vertex indices of the soup's triangles
+ *            (same order and orientation), or NULL; needs tri_keys.
+ * n_verts:   one int64 written with the number of vertices; more than
+ *            capacity_verts gives GH_ERR_CAPACITY as for triangles.
+ * Supported by gh_polygonize and gh_polygonize_batch with GH_METHOD_HOP. */
 typedef struct {
     float *tri_xyz;
     uint64_t *tri_keys;
@@ -176,6 +190,10 @@ typedef struct {
     int64_t capacity_cells;
     int64_t *n_cells;
     gh_stats *stats;
+    float *vert_xyz;
+    int32_t *tri_idx;
+    int64_t capacity_verts;
+    int64_t *n_verts;
 } gh_mesh;
 
 /* Creates an SDB from a host blob (formats above).  Copies the blob to the

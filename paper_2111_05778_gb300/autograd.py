@@ -18,8 +18,8 @@ class _ImplicitPolygonize(torch.autograd.Function):
     def forward(ctx, params, width, n_mid, N, lo, hi, r0, alpha, beta, lam, precision):
         sdb = gh.MlpSdb(params.detach().cpu().numpy(), width, n_mid, r0, alpha, beta, lam)
         eps = sdb.calibrate(N, lo, hi) if precision == "bf16" else None
-        mesh = gh.polygonize(sdb, N, lo=lo, hi=hi, precision=precision, keys=True, eps=eps)
-        verts, faces, _ = gh.unique_vertices(mesh)
+        mesh = gh.polygonize(sdb, N, lo=lo, hi=hi, precision=precision, eps=eps, indexed=True)
+        verts, faces = mesh.verts, mesh.faces.long()
         ctx.sdb = sdb
         ctx.save_for_backward(verts)
         ctx.mark_non_differentiable(faces)
@@ -36,8 +36,8 @@ class _ImplicitPolygonizeCsg(torch.autograd.Function):
     @staticmethod
     def forward(ctx, prims, N, lo, hi):
         sdb = gh.CsgSdb(prims.detach().cpu().double().numpy())
-        mesh = gh.polygonize(sdb, N, lo=lo, hi=hi, keys=True)
-        verts, faces, _ = gh.unique_vertices(mesh)
+        mesh = gh.polygonize(sdb, N, lo=lo, hi=hi, indexed=True)
+        verts, faces = mesh.verts, mesh.faces.long()
         ctx.sdb = sdb
         ctx.shape = prims.shape
         ctx.dtype = prims.dtype

@@ -395,7 +395,7 @@ extern "C" int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out) {
 static void free_scratch(gh_sdb *s) {
     Scratch &c = s->scr;
     void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat};
+                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->scr = Scratch{};
@@ -426,6 +426,7 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     free_scratch(s);
     c.lat = keep_lat;
     c.cap_lat = keep_cap;
+    s->item_valid = false;
     const long long ncols = (long long)NN * NN, nlines = (long long)(NN + 1) * (NN + 1);
     GH_CUDA(cudaMalloc((void **)&c.ctr, sizeof(Counters)));
     GH_CUDA(cudaMalloc((void **)&c.marks_raw, sizeof(unsigned long long) * cm));
@@ -444,6 +445,24 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     s->scr_N = NN;
     return GH_OK;
 }
+
+// The vertex numbering of the indexed mesh output (one entry per list slot).
+static int ensure_index(gh_sdb *s) {
+    Scratch &c = s->scr;
+    if (c.cap_index >= c.cap_verts && c.ebase) return GH_OK;
+    if (c.ebase) cudaFree(c.ebase);
+    if (c.ebsum) cudaFree(c.ebsum);
+    c.ebase = nullptr;
+    c.ebsum = nullptr;
+    c.cap_index = 0;
+    GH_CUDA(cudaMalloc((void **)&c.ebase, sizeof(uint32_t) * (c.cap_verts + 1)));
+    GH_CUDA(cudaMalloc((void **)&c.ebsum, sizeof(uint32_t) * scan_partials(c.cap_verts)));
+    c.cap_index = c.cap_verts;
+    s->item_valid = false;
+    return GH_OK;
+}
+
+static bool wants_index(const gh_mesh &m) { return m.vert_xyz != nullptr || m.tri_idx != nullptr; }
 
 // The dense lattice array of the enumeration method.
 static int ensure_lattice(gh_sdb *s, int N) {
@@ -514,6 +533,8 @@ static int check_mesh(const gh_mesh *m) {
         return fail(GH_ERR_ARG, "mesh: tri_xyz is NULL or capacity negative");
     if (m->cell_ids && (!m->cell_cases || m->capacity_cells < 0))
         return fail(GH_ERR_ARG, "mesh: cell_ids given without cell_cases / capacity");
+    if (m->tri_idx && !m->tri_keys) return fail(GH_ERR_ARG, "mesh: tri_idx needs tri_keys");
+    if (m->vert_xyz && m->capacity_verts < 0) return fail(GH_ERR_ARG, "mesh: capacity_verts negative");
     return GH_OK;
 }
 
@@ -613,6 +634,7 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
         launches += LAUNCHES_REFINE;
     }
     launch_mc(g, c, out, nsm, st);
+    if (wants_index(out)) launch_index_mesh(g, c, out, nsm, st);
     launch_finalize(c, out, (long long)g.N * g.N, st);
     mark_phase(6, st);
     g_prof.recorded = g_prof.enabled;
@@ -634,6 +656,8 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
     if (o.method != GH_METHOD_HOP && o.method != GH_METHOD_ENUM) return fail(GH_ERR_ARG, "unknown method %d", o.method);
     if (o.method == GH_METHOD_ENUM && o.precision != GH_FP32)
         return fail(GH_ERR_UNIMPLEMENTED, "the enumeration method runs in FP32 only");
+    if (o.method == GH_METHOD_ENUM && wants_index(*out))
+        return fail(GH_ERR_UNIMPLEMENTED, "the indexed mesh output needs GH_METHOD_HOP");
     if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
         return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
     if (o.precision == GH_BF16_REFINE) {
@@ -657,6 +681,7 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = ensure_scratch(s, g.N, want_m, want_v))) return rc;
         if (o.method == GH_METHOD_ENUM && (rc = ensure_lattice(s, g.N))) return rc;
+        if (wants_index(*out) && (rc = ensure_index(s))) return rc;
         if ((rc = enqueue_once(s, g, o, *out, nsm, st))) return rc;
         if (!o.sync) return GH_OK;
         Counters c;
@@ -676,6 +701,10 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         if (out->cell_ids && c.cells > (unsigned long long)out->capacity_cells)
             return fail(GH_ERR_CAPACITY, "cell buffer holds %lld, %llu needed", (long long)out->capacity_cells,
                         c.cells);
+        if (c.flags & FLAG_INDEX_MISS) return fail(GH_ERR_CUDA, "indexed output: a triangle edge was not listed");
+        if (out->vert_xyz && c.mesh_verts > (unsigned long long)out->capacity_verts)
+            return fail(GH_ERR_CAPACITY, "vertex buffer holds %lld, %llu needed", (long long)out->capacity_verts,
+                        c.mesh_verts);
         return GH_OK;
     }
     return fail(GH_ERR_CAPACITY, "internal scratch kept overflowing");
@@ -834,6 +863,7 @@ static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_
     }
     for (int b = 0; b < B; ++b) {
         launch_mc(P.g[b], sd[b]->scr, outs[b], nsm, st);
+        if (wants_index(outs[b])) launch_index_mesh(P.g[b], sd[b]->scr, outs[b], nsm, st);
         launch_finalize(sd[b]->scr, outs[b], (long long)P.g[b].N * P.g[b].N, st);
     }
     GH_CUDA(cudaGetLastError());
@@ -904,7 +934,8 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
     const bool sync = o.sync || graph;
     for (int attempt = 0; attempt < 4; ++attempt) {
         for (int b = 0; b < B; ++b)
-            if ((rc = ensure_scratch(sd[b], P.g[b].N, want_m[b], want_v[b]))) {
+            if ((rc = ensure_scratch(sd[b], P.g[b].N, want_m[b], want_v[b])) ||
+                (wants_index(outs[b]) && (rc = ensure_index(sd[b])))) {
                 cudaFree(d_items);
                 return rc;
             }
@@ -942,6 +973,11 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
                           (long long)outs[b].capacity_tris, c.tris);
             else if (outs[b].cell_ids && c.cells > (unsigned long long)outs[b].capacity_cells)
                 rc = fail(GH_ERR_CAPACITY, "item %d: cell buffer too small", b);
+            else if (c.flags & FLAG_INDEX_MISS)
+                rc = fail(GH_ERR_CUDA, "item %d: indexed output: a triangle edge was not listed", b);
+            else if (outs[b].vert_xyz && c.mesh_verts > (unsigned long long)outs[b].capacity_verts)
+                rc = fail(GH_ERR_CAPACITY, "item %d: vertex buffer holds %lld, %llu needed", b,
+                          (long long)outs[b].capacity_verts, c.mesh_verts);
         }
         if (rc || !graph) {
             cudaFree(d_items);
@@ -1095,6 +1131,7 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     if (n_prim < 1 || n_prim > GH_MAX_PRIMS)
         return fail(GH_ERR_ARG, "gh_polygonize_csg_noalloc: n_prim = %d outside [1, %d]", n_prim, GH_MAX_PRIMS);
     if ((rc = check_mesh(out))) return rc;
+    if (wants_index(*out)) return fail(GH_ERR_UNIMPLEMENTED, "gh_polygonize_csg_noalloc: no indexed mesh output");
     int dev, nsm;
     if ((rc = ensure_device(&dev, &nsm))) return rc;
     void *base = nullptr;

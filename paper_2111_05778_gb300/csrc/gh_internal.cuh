@@ -21,7 +21,8 @@ struct Counters {
     unsigned long long next_tile;  // work counter of point-list kernels
     unsigned long long next_tile2; // second work counter (refinement pass)
     unsigned long long row_slots;  // rows the neural hopper ran (live or not): 128 per tile-step
-    unsigned long long pad[5];
+    unsigned long long mesh_verts; // indexed output: crossing lattice edges
+    unsigned long long pad[4];
 };
 
 enum : unsigned long long {
@@ -31,6 +32,7 @@ enum : unsigned long long {
     FLAG_CELL_OVERFLOW = 8ull,   // caller's cell buffer too small
     FLAG_NONFINITE = 16ull,      // f was NaN or inf somewhere
     FLAG_TIMEOUT = 32ull,        // a bounded device wait gave up
+    FLAG_INDEX_MISS = 64ull,     // indexed output: a triangle edge without a listed end point
 };
 
 // Grid parameters as the kernels see them (FP32).
@@ -84,6 +86,9 @@ struct Scratch {
     long long cap_marks, cap_verts;
     float *lat;                     // enumeration: f at all (N+1)^3 lattice points
     long long cap_lat;
+    uint32_t *ebase;                // indexed output: first mesh vertex of each list entry [cap_verts + 1]
+    uint32_t *ebsum;                // its scan partials
+    long long cap_index;            // entries ebase was sized for (0: none)
 };
 
 // One polygonization of a batch: grid, scratch and SDB.  Kernels that serve
@@ -136,6 +141,13 @@ void launch_eval_vertices_mlp_bf16(const Item *items, int n_items, int width, in
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
 void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);  // k_pipeline.cu
+// exclusive scan of n uint32 into out[0..n] (k_pipeline.cu); bsum holds
+// ceil(n / 4096) partials; *total gets the sum
+void scan_u32_dev(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
+                  Counters *ctr, cudaStream_t st);
+long long scan_partials(long long n);
+// indexed mesh output after Marching Cubes (k_index.cu)
+void launch_index_mesh(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
 
 // implicit-surface adjoint (k_adjoint.cu)
 struct AdjBuffers {

@@ -333,6 +333,13 @@ static void scan_u32(const uint32_t *in, long long n, uint32_t *out, uint32_t *b
     k_scan_apply<<<nb, SCAN_T, 0, st>>>(in, n, bsum, out, total, ctr);
 }
 
+void scan_u32_dev(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
+                  Counters *ctr, cudaStream_t st) {
+    scan_u32(in, n, out, bsum, total, ctr, st);
+}
+
+long long scan_partials(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
 // ---------------------------------------------------------------------------
 // Marks grouped by column.
 // ---------------------------------------------------------------------------
@@ -802,7 +809,10 @@ __global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
     if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) status = GH_ERR_CAPACITY;
     if (c.tris > (unsigned long long)out.capacity_tris) status = GH_ERR_CAPACITY;
     if (out.cell_ids && c.cells > (unsigned long long)out.capacity_cells) status = GH_ERR_CAPACITY;
+    if (out.vert_xyz && c.mesh_verts > (unsigned long long)out.capacity_verts) status = GH_ERR_CAPACITY;
+    if (c.flags & FLAG_INDEX_MISS) status = GH_ERR_CUDA;
     if (out.n_tris) *out.n_tris = (long long)c.tris;
+    if (out.n_verts) *out.n_verts = (long long)c.mesh_verts;
     if (out.n_cells) *out.n_cells = (long long)c.cells;
     if (out.stats) {
         gh_stats *st = out.stats;
@@ -815,6 +825,7 @@ __global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
         st->surface_cells = (long long)c.cells;
         st->triangles = (long long)c.tris;
         st->row_slots = (long long)c.row_slots;
+        st->mesh_vertices = (long long)c.mesh_verts;
     }
 }
 

@@ -49,17 +49,19 @@ class Options(ctypes.Structure):
 
 
 STAT_FIELDS = ["status", "columns", "hop_evals", "marked_cells", "unique_vertices", "refined_vertices",
-               "surface_cells", "triangles", "row_slots"]
+               "surface_cells", "triangles", "row_slots", "mesh_vertices"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 7)]
+    _fields_ = [(n, ctypes.c_int64) for n in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 6)]
 
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("tri_xyz", ctypes.c_void_p), ("tri_keys", ctypes.c_void_p), ("capacity_tris", ctypes.c_int64),
                 ("n_tris", ctypes.c_void_p), ("cell_ids", ctypes.c_void_p), ("cell_cases", ctypes.c_void_p),
-                ("capacity_cells", ctypes.c_int64), ("n_cells", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+                ("capacity_cells", ctypes.c_int64), ("n_cells", ctypes.c_void_p), ("stats", ctypes.c_void_p),
+                ("vert_xyz", ctypes.c_void_p), ("tri_idx", ctypes.c_void_p), ("capacity_verts", ctypes.c_int64),
+                ("n_verts", ctypes.c_void_p)]
 
 
 class Profile(ctypes.Structure):
@@ -235,14 +237,18 @@ class MlpSdb(Sdb):
 # ---------------------------------------------------------------------------
 class Mesh:
     """Triangle soup on the device: tri_xyz [T,3,3] float32, tri_keys [T,3]
-    int64 edge keys (optional), surface cells (optional) and statistics."""
+    int64 edge keys (optional), surface cells (optional), statistics, and
+    (indexed=True) the indexed mesh: verts [V,3] float32 and faces [T,3] int32
+    into them, in the soup's triangle order."""
 
-    def __init__(self, tri_xyz, tri_keys, cell_ids, cell_cases, stats):
+    def __init__(self, tri_xyz, tri_keys, cell_ids, cell_cases, stats, verts=None, faces=None):
         self.tri_xyz = tri_xyz
         self.tri_keys = tri_keys
         self.cell_ids = cell_ids
         self.cell_cases = cell_cases
         self.stats = stats
+        self.verts = verts
+        self.faces = faces
 
     @property
     def n_tris(self):
@@ -252,17 +258,22 @@ class Mesh:
 class Buffers:
     """Caller-owned device buffers of one polygonization (reusable)."""
 
-    def __init__(self, cap_tris, keys=False, cap_cells=0, device=None):
+    def __init__(self, cap_tris, keys=False, cap_cells=0, device=None, cap_verts=0):
         import torch
 
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.cap_tris = int(cap_tris)
         self.cap_cells = int(cap_cells)
+        self.cap_verts = int(cap_verts)
+        if cap_verts:
+            keys = True  # the face indices are derived from the edge keys
         self.tri_xyz = torch.empty((max(self.cap_tris, 1), 3, 3), dtype=torch.float32, device=dev)
         self.tri_keys = torch.empty((max(self.cap_tris, 1), 3), dtype=torch.int64, device=dev) if keys else None
         self.cell_ids = torch.empty(max(self.cap_cells, 1), dtype=torch.int64, device=dev) if cap_cells else None
         self.cell_cases = torch.empty(max(self.cap_cells, 1), dtype=torch.uint8, device=dev) if cap_cells else None
-        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)  # n_tris, n_cells
+        self.verts = torch.empty((max(self.cap_verts, 1), 3), dtype=torch.float32, device=dev) if cap_verts else None
+        self.faces = torch.empty((max(self.cap_tris, 1), 3), dtype=torch.int32, device=dev) if cap_verts else None
+        self.counts = torch.zeros(3, dtype=torch.int64, device=dev)  # n_tris, n_cells, n_verts
         self.stats = torch.zeros(16, dtype=torch.int64, device=dev)
         self.desc = MeshDesc()
         d = self.desc
@@ -275,6 +286,10 @@ class Buffers:
         d.capacity_cells = self.cap_cells
         d.n_cells = self.counts.data_ptr() + 8
         d.stats = self.stats.data_ptr()
+        d.vert_xyz = self.verts.data_ptr() if cap_verts else None
+        d.tri_idx = self.faces.data_ptr() if cap_verts else None
+        d.capacity_verts = self.cap_verts
+        d.n_verts = self.counts.data_ptr() + 16
 
     def stats_dict(self):
         v = self.stats.cpu().numpy()
@@ -308,22 +323,26 @@ def polygonize_into(sdb: Sdb, N, bufs: Buffers, lo=-1.0, hi=1.0, precision="fp32
 
 
 def polygonize(sdb: Sdb, N, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_DIAGONAL, keys=False, cells=False,
-               eps=None, stream=None, method="hop") -> Mesh:
+               eps=None, stream=None, method="hop", indexed=False) -> Mesh:
     """gh_polygonize with buffers sized (and re-sized) automatically; returns
-    device tensors trimmed to the produced counts."""
-    key = (int(N), bool(keys), bool(cells))
+    device tensors trimmed to the produced counts.  indexed=True also returns
+    the on-device indexed mesh (Mesh.verts, Mesh.faces)."""
+    keys = bool(keys) or bool(indexed)
+    key = (int(N), keys, bool(cells), bool(indexed))
     cap = sdb._cap.get(key, 4 * int(N) * int(N) + 4096)
     for _ in range(3):
-        bufs = Buffers(cap, keys=keys, cap_cells=cap if cells else 0)
+        capv = cap // 2 + 4096 if indexed else 0
+        bufs = Buffers(cap, keys=keys, cap_cells=cap if cells else 0, cap_verts=capv)
         rc = polygonize_into(sdb, N, bufs, lo, hi, precision, tau_mode, eps, True, stream, method=method)
         counts = bufs.counts.cpu().numpy()
         if rc == GH_OK:
             sdb._cap[key] = cap
-            T, C = int(counts[0]), int(counts[1])
+            T, C, V = int(counts[0]), int(counts[1]), int(counts[2])
             return Mesh(bufs.tri_xyz[:T], bufs.tri_keys[:T] if keys else None,
                         bufs.cell_ids[:C] if cells else None, bufs.cell_cases[:C] if cells else None,
-                        bufs.stats_dict())
-        cap = int(max(counts[0], counts[1]) * 1.1) + 4096
+                        bufs.stats_dict(), bufs.verts[:V] if indexed else None,
+                        bufs.faces[:T] if indexed else None)
+        cap = int(max(counts[0], counts[1], 2 * counts[2]) * 1.1) + 4096
     raise GhError(GH_ERR_CAPACITY, "output buffers kept overflowing")
 
 
@@ -333,11 +352,11 @@ class Batch:
     graph of the same launches that replay() re-runs."""
 
     def __init__(self, sdbs, Ns, caps, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0,
-                 mlp_tiles=0):
+                 mlp_tiles=0, indexed=False):
         self.sdbs = list(sdbs)
         self.Ns = [int(n) for n in Ns]
         self.B = len(self.sdbs)
-        self.bufs = [Buffers(c, keys=keys) for c in caps]
+        self.bufs = [Buffers(c, keys=keys, cap_verts=(c // 2 + 4096) if indexed else 0) for c in caps]
         self.grids = (Grid * self.B)(*[_grid(n, lo, hi) for n in self.Ns])
         self.handles = (ctypes.c_void_p * self.B)(*[s_.handle for s_ in self.sdbs])
         self.meshes = (MeshDesc * self.B)(*[b.desc for b in self.bufs])
@@ -376,21 +395,24 @@ class Batch:
     def counts(self):
         import torch
 
-        return torch.stack([b.counts[0] for b in self.bufs]).cpu().numpy()
+        # triangles needed, or twice the mesh vertices when those overflowed
+        return torch.stack([torch.maximum(b.counts[0], 2 * b.counts[2]) for b in self.bufs]).cpu().numpy()
 
     def mesh(self, b) -> "Mesh":
-        T = int(self.bufs[b].counts[0].item())
         bb = self.bufs[b]
+        T, _, V = [int(x) for x in bb.counts.cpu().numpy()]
+        ind = bb.verts is not None
         return Mesh(bb.tri_xyz[:T], bb.tri_keys[:T] if bb.tri_keys is not None else None, None, None,
-                    bb.stats_dict())
+                    bb.stats_dict(), bb.verts[:V] if ind else None, bb.faces[:T] if ind else None)
 
 
-def polygonize_batch(sdbs, Ns, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0, mlp_tiles=0):
+def polygonize_batch(sdbs, Ns, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0, mlp_tiles=0,
+                     indexed=False):
     """gh_polygonize_batch with per-item buffers sized automatically; returns
     the Batch (its meshes via .mesh(b))."""
     caps = [4 * n * n + 4096 for n in Ns]
     for _ in range(3):
-        bt = Batch(sdbs, Ns, caps, lo, hi, precision, keys, eps, ray_block, mlp_tiles)
+        bt = Batch(sdbs, Ns, caps, lo, hi, precision, keys, eps, ray_block, mlp_tiles, indexed)
         rc = bt.run(sync=True)
         if rc == GH_OK:
             return bt
