@@ -541,8 +541,10 @@ def run_adjoint(args):
 
 def run_crossover(args):
     """Grid hopping against enumeration (Sec. 2: every lattice point and cell)
-    on the same GPU, for the analytic scene and the width-256 network, over N
-    (the paper's Sec. 5 comparison, here with both methods on the GB300)."""
+    on the same GPU, for the analytic scene, the width-256 network and a
+    network of the paper's own architecture (8 layers of width 64, batch
+    normalisation folded, lambda = 1.5), over N (the paper's Sec. 5
+    comparisons, here with both methods on the GB300)."""
     import torch
 
     from paper_2111_05778_gb300 import gh, synth
@@ -551,8 +553,10 @@ def run_crossover(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     rows = []
+    pp, pw, pl, plam, _ = synth.paper_network(0)
     cases = [("csg", gh.CsgSdb(synth.csg_prims(0)), (64, 128, 256, 512, 1024)),
-             ("mlp256", gh.MlpSdb(synth.mlp_params(1, 256), 256), (64, 128, 256, 512))]
+             ("mlp256", gh.MlpSdb(synth.mlp_params(1, 256), 256), (64, 128, 256, 512)),
+             ("paper_net_8x64_bn", gh.paper_mlp(pp, pw, pl, plam), (64, 128, 256, 512))]
     for name, sdb, Ns in cases:
         for N in Ns:
             res = {"sdb": name, "N": N}

@@ -91,12 +91,18 @@ typedef struct {
  * { W[width][width] b[width] } then w_out[width] b_out[1] (row-major,
  * out x in, like torch.nn.Linear).  g = w_out . relu(W_mid ... relu(W0 p + b0)
  * ...) + b_out and f(p) = (|p| - r0 + alpha g(p)) / beta / lipschitz_scale.
- * width must be 64, 128 or 256. */
+ * flags = GH_MLP_NO_RADIAL drops the |p| term: f = (alpha g - r0) / beta /
+ * lipschitz_scale, the form of the paper's own networks (SDB = network /
+ * lambda, Sec. 5.2; alpha = beta = 1, r0 = 0).  A network trained with batch
+ * normalisation is passed with the normalisation folded into the preceding
+ * layer.  width must be 64, 128 or 256. */
 typedef struct {
     int32_t width, n_mid;
-    int32_t reserved[2];
+    int32_t flags;
+    int32_t reserved;
     float r0, alpha, beta, reserved_f;
 } gh_mlp_header;
+#define GH_MLP_NO_RADIAL 1
 
 typedef struct gh_sdb gh_sdb; /* opaque; owned by the library */
 

@@ -55,7 +55,7 @@ def lib():
             L.or_csg_new.restype = P
             L.or_csg_new.argtypes = [I, P]
             L.or_mlp_new.restype = P
-            L.or_mlp_new.argtypes = [I, I, P, D, D, D, D]
+            L.or_mlp_new.argtypes = [I, I, P, D, D, D, D, D]
             L.or_lattice_new.restype = P
             L.or_lattice_new.argtypes = [I, P, D, P]
             L.or_sdb_free.argtypes = [P]
@@ -157,13 +157,14 @@ def mlp_param_count(width: int, nmid: int) -> int:
     return 3 * width + width + nmid * (width * width + width) + width + 1
 
 
-def mlp(width, nmid, params, r0=0.6, alpha=0.1, beta=1.1, lam=1.0) -> SDB:
-    """params: packed W0[W,3] b0[W] {W[W,W] b[W]}*nmid wout[W] bout (float64)."""
+def mlp(width, nmid, params, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True) -> SDB:
+    """params: packed W0[W,3] b0[W] {W[W,W] b[W]}*nmid wout[W] bout (float64).
+    radial=False drops the |p| term: f = (alpha g - r0) / beta / lam."""
     a = np.ascontiguousarray(params, dtype=np.float64).ravel()
     n = mlp_param_count(width, nmid)
     if a.size != n:
         raise ValueError("expected %d parameters, got %d" % (n, a.size))
-    h = lib().or_mlp_new(width, nmid, _ptr(a), r0, alpha, beta, lam)
+    h = lib().or_mlp_new(width, nmid, _ptr(a), r0, alpha, beta, lam, 1.0 if radial else 0.0)
     return SDB(h, "mlp", n)
 
 
@@ -314,14 +315,16 @@ def np_forward(layers, P):
     return zs, g
 
 
-def np_eval(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
-    """f(p) = (|p| - r0 + alpha g(p)) / beta / lam at the rows of P (Sec. 5.2)."""
+def np_eval(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True):
+    """f(p) = (|p| - r0 + alpha g(p)) / beta / lam at the rows of P (Sec. 5.2);
+    radial=False drops |p|."""
     P = np.asarray(P, np.float64).reshape(-1, 3)
     _, g = np_forward(np_layers(params, width, nmid), P)
-    return (np.linalg.norm(P, axis=1) - r0 + alpha * g) / beta / lam
+    rad = 1.0 if radial else 0.0
+    return (rad * np.linalg.norm(P, axis=1) - r0 + alpha * g) / beta / lam
 
 
-def np_grad_x(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+def np_grad_x(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True):
     P = np.asarray(P, np.float64).reshape(-1, 3)
     layers = np_layers(params, width, nmid)
     zs, _ = np_forward(layers, P)
@@ -330,10 +333,11 @@ def np_grad_x(params, width, nmid, P, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
         d = (d @ layers[l][0]) * (zs[l - 1] > 0)
     dgdp = d @ layers[0][0]
     r = np.linalg.norm(P, axis=1, keepdims=True)
-    return (P / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
+    rad = 1.0 if radial else 0.0
+    return (rad * P / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
 
 
-def np_adjoint(params, width, nmid, V, dLdv, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+def np_adjoint(params, width, nmid, V, dLdv, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True):
     """Implicit-surface adjoint sum_v s_v df/dtheta(v) with
     s_v = -(dL/dv . grad_x f)/|grad_x f|^2, packed like the parameters."""
     V = np.asarray(V, np.float64).reshape(-1, 3)
@@ -348,7 +352,8 @@ def np_adjoint(params, width, nmid, V, dLdv, r0=0.6, alpha=0.1, beta=1.1, lam=1.
         ds[l - 1] = d
     dgdp = ds[0] @ layers[0][0]
     r = np.linalg.norm(V, axis=1, keepdims=True)
-    gx = (V / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
+    rad = 1.0 if radial else 0.0
+    gx = (rad * V / np.where(r > 0, r, 1.0) + alpha * dgdp) / (beta * lam)
     s = -(G * gx).sum(1) / (gx * gx).sum(1)
     c = alpha / (beta * lam)
     out = []

@@ -63,7 +63,8 @@ typedef struct {
     double *W0, *b0;   /* [width,3], [width] */
     double **Wm, **bm; /* nmid x [width,width], nmid x [width] */
     double *wout, bout;
-    double r0, alpha, beta, lam; /* f = (|p| - r0 + alpha g) / beta / lam */
+    double r0, alpha, beta, lam; /* f = (rad |p| - r0 + alpha g) / beta / lam */
+    double rad;                  /* 1, or 0 for a network without the radial term */
     /* lattice: trilinear interpolation of given values at the lattice points
      * of a grid (a test device for Marching Cubes, not an SDB in general) */
     int ln;
@@ -186,7 +187,10 @@ static double csg_eval(const osdb *s, const double *p) {
 }
 
 /* Neural SDB (Sec. 5.2, Eq. 7): a ReLU MLP g, used as
- * f(p) = (|p| - r0 + alpha g(p)) / beta, then shrunk by lambda.
+ * f(p) = (|p| - r0 + alpha g(p)) / beta, then shrunk by lambda; a network
+ * given without the radial term (rad = 0, the paper's own networks of
+ * Sec. 5.2, where the SDB is the network's output divided by lambda) drops
+ * |p|.
  * If acts != NULL the pre-activations z_l of every hidden layer are stored
  * there, layer after layer, (1 + nmid) * width doubles. */
 static double mlp_g(const osdb *s, const double *p, double *acts) {
@@ -240,7 +244,7 @@ static double sdb_eval(const osdb *s, const double *p) {
     if (s->kind == 0) return csg_eval(s, p);
     if (s->kind == 2) return lattice_eval(s, p);
     double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    return (r - s->r0 + s->alpha * mlp_g(s, p, NULL)) / s->beta / s->lam;
+    return (s->rad * r - s->r0 + s->alpha * mlp_g(s, p, NULL)) / s->beta / s->lam;
 }
 
 void *or_csg_new(int nprim, const double *prims) {
@@ -255,7 +259,7 @@ void *or_csg_new(int nprim, const double *prims) {
 
 /* params: W0[W*3] b0[W] { Wl[W*W] bl[W] } x nmid  wout[W] bout */
 void *or_mlp_new(int width, int nmid, const double *params, double r0, double alpha, double beta,
-                 double lam) {
+                 double lam, double rad) {
     osdb *s = (osdb *)calloc(1, sizeof(osdb));
     int W = width;
     size_t n = (size_t)W * 3 + W + (size_t)nmid * ((size_t)W * W + W) + W + 1;
@@ -281,6 +285,7 @@ void *or_mlp_new(int width, int nmid, const double *params, double r0, double al
     s->alpha = alpha;
     s->beta = beta;
     s->lam = lam;
+    s->rad = rad;
     s->prim = buf; /* owner of the parameter block */
     return s;
 }
@@ -749,8 +754,8 @@ void *or_hop(const void *hs, int N, const double *lo, double h, double tau, doub
 /* Gradients of the neural SDB (implicit-surface adjoint)                   */
 /* ------------------------------------------------------------------------ */
 /*
- * For f(p; theta) = (|p| - r0 + alpha g(p; theta)) / (beta lam):
- *   grad_x f = (p/|p| + alpha dg/dp) / (beta lam)
+ * For f(p; theta) = (rad |p| - r0 + alpha g(p; theta)) / (beta lam):
+ *   grad_x f = (rad p/|p| + alpha dg/dp) / (beta lam)
  *   df/dtheta = alpha dg/dtheta / (beta lam)
  * by back-propagation through the ReLU layers.  A vertex v on the level set
  * f = 0 moves with theta as dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2,
@@ -804,7 +809,7 @@ static void mlp_grads(const osdb *s, const double *p, double *gx, double *gth, d
     }
     double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     for (int a = 0; a < 3; ++a)
-        gx[a] = ((r > 0 ? p[a] / r : 0.0) + s->alpha * dgp[a]) / (s->beta * s->lam);
+        gx[a] = (s->rad * (r > 0 ? p[a] / r : 0.0) + s->alpha * dgp[a]) / (s->beta * s->lam);
     free(z);
     free(dl);
 }

@@ -283,6 +283,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     if (W != 64 && W != 128 && W != 256) return fail(GH_ERR_ARG, "MLP width %d not in {64, 128, 256}", W);
     if (h.n_mid < 1 || h.n_mid > 16) return fail(GH_ERR_ARG, "MLP n_mid %d outside [1, 16]", h.n_mid);
     if (!(h.beta > 0) || !isfinite(h.r0) || !isfinite(h.alpha)) return fail(GH_ERR_ARG, "MLP header values invalid");
+    if (h.flags & ~GH_MLP_NO_RADIAL) return fail(GH_ERR_ARG, "MLP header: unknown flags 0x%x", h.flags);
     const int64_t np = gh_mlp_param_count(W, h.n_mid);
     if (d->blob_bytes != sizeof(h) + (size_t)np * sizeof(float))
         return fail(GH_ERR_ARG, "MLP blob has %zu bytes, expected %zu", d->blob_bytes, sizeof(h) + (size_t)np * 4);
@@ -351,6 +352,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.width = W;
     m.n_mid = h.n_mid;
     m.r0 = h.r0;
+    m.radial = (h.flags & GH_MLP_NO_RADIAL) ? 0.f : 1.f;
     m.alpha = h.alpha;
     m.beta = h.beta;
     m.inv_lam = 1.f / s->lam;

@@ -59,6 +59,7 @@ static_assert(sizeof(Prim) == 80, "Prim layout");
 struct MlpDev {
     int width, n_mid;
     float r0, alpha, beta, inv_lam;
+    float radial;  // 1, or 0 without the |p| term (GH_MLP_NO_RADIAL)
     const float *w0;    // [W][3]
     const float *b0;    // [W]
     const float *wt;    // n_mid x [W(in)][W(out)] transposed FP32 hidden weights

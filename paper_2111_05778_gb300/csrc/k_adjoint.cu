@@ -4,7 +4,8 @@
 // parameters as dv/dtheta = -grad_x f (df/dtheta) / |grad_x f|^2, so a loss on
 // the vertices has
 //   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f(v)) / |grad_x f(v)|^2.
-// For f = (|p| - r0 + alpha g(p)) / (beta lambda) and g a ReLU MLP
+// For f = (rad |p| - r0 + alpha g(p)) / (beta lambda) (rad = 0 for a network
+// given without the radial term) and g a ReLU MLP
 //   z_0 = W_0 p + b_0, z_l = W_l relu(z_{l-1}) + b_l (l = 1..L), g = w . relu(z_L) + b,
 // back-propagation gives delta_L = w * [z_L > 0], delta_{l-1} = (W_l^T delta_l) *
 // [z_{l-1} > 0], dg/dp = W_0^T delta_0, and with c = alpha / (beta lambda)
@@ -139,7 +140,7 @@ __global__ void k_adj_top(const float *__restrict__ ZL, int V, const float *__re
 // grad_x f from delta_0, then s_v
 __global__ void k_adj_s(const float *__restrict__ P, const float *__restrict__ dL, int V,
                         const float *__restrict__ D0, const float *__restrict__ w0, int W, float alpha, float inv_bl,
-                        float *__restrict__ s) {
+                        float radial, float *__restrict__ s) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int v = warp; v < V; v += nw) {
@@ -158,7 +159,7 @@ __global__ void k_adj_s(const float *__restrict__ P, const float *__restrict__ d
         if (lane == 0) {
             const float px = P[3 * v], py = P[3 * v + 1], pz = P[3 * v + 2];
             const float r = sqrtf(px * px + py * py + pz * pz);
-            const float ir = r > 0.f ? 1.f / r : 0.f;
+            const float ir = r > 0.f ? radial / r : 0.f;
             const float fx = (px * ir + alpha * gx) * inv_bl;
             const float fy = (py * ir + alpha * gy) * inv_bl;
             const float fz = (pz * ir + alpha * gz) * inv_bl;
@@ -212,7 +213,7 @@ void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, floa
     for (int l = L; l >= 1; --l)
         gemm<false, false, false, false>(V, W, W, Dl[l], W, m.wmid + (size_t)(l - 1) * W * W, W, Dl[l - 1], W,
                                          nullptr, Zl[l - 1], nullptr, 1, st);
-    k_adj_s<<<(V + 7) / 8, 256, 0, st>>>(P, dL, V, Dl[0], m.w0, W, m.alpha, 1.f / m.beta * m.inv_lam, b.s);
+    k_adj_s<<<(V + 7) / 8, 256, 0, st>>>(P, dL, V, Dl[0], m.w0, W, m.alpha, 1.f / m.beta * m.inv_lam, m.radial, b.s);
     // parameter gradients: sums over the vertices of the chunk
     const size_t oW0 = 0, ob0 = (size_t)3 * W, omid = ob0 + W;
     const size_t ow = omid + (size_t)L * ((size_t)W * W + W);

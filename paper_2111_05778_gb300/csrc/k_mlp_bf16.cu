@@ -198,7 +198,7 @@ __device__ __forceinline__ bool epi_any(int id, bool v) {
 
 __device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, float z, float g) {
     const float r = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
-    return (fmaf(m.alpha, g, r - m.r0) / m.beta) * m.inv_lam;
+    return (fmaf(m.alpha, g, m.radial * r - m.r0) / m.beta) * m.inv_lam;
 }
 
 // ---------------------------------------------------------------------------

@@ -155,7 +155,7 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
 
 __device__ __forceinline__ float outer_f(const MlpDev &m, float4 p, float g) {
     const float r = sqrtf(fmaf(p.x, p.x, fmaf(p.y, p.y, p.z * p.z)));
-    return (fmaf(m.alpha, g, r - m.r0) / m.beta) * m.inv_lam;
+    return (fmaf(m.alpha, g, m.radial * r - m.r0) / m.beta) * m.inv_lam;
 }
 
 // Persistent hopper over a batch of items: the CTA's 128 rows take columns

@@ -196,6 +196,12 @@ def csg_blob(prims) -> bytes:
     return hdr.tobytes() + rec.tobytes()
 
 
+def paper_mlp(params, width, n_mid, lam=1.5) -> "MlpSdb":
+    """A network in the paper's form (Sec. 5.2): SDB = network / lambda, no
+    radial term, batch normalisation already folded into the weights."""
+    return MlpSdb(params, width, n_mid, r0=0.0, alpha=1.0, beta=1.0, lam=lam, radial=False)
+
+
 class CsgSdb(Sdb):
     kind = GH_SDB_CSG
 
@@ -204,23 +210,28 @@ class CsgSdb(Sdb):
         super().__init__(csg_blob(self.prims), 1.0)
 
 
-def mlp_blob(params, width, n_mid, r0, alpha, beta) -> bytes:
+GH_MLP_NO_RADIAL = 1
+
+
+def mlp_blob(params, width, n_mid, r0, alpha, beta, radial=True) -> bytes:
     p = np.ascontiguousarray(params, np.float32).ravel()
-    hdr = np.array([width, n_mid, 0, 0], np.int32).tobytes() + np.array([r0, alpha, beta, 0], np.float32).tobytes()
+    flags = 0 if radial else GH_MLP_NO_RADIAL
+    hdr = np.array([width, n_mid, flags, 0], np.int32).tobytes() + np.array([r0, alpha, beta, 0], np.float32).tobytes()
     return hdr + p.tobytes()
 
 
 class MlpSdb(Sdb):
     kind = GH_SDB_MLP
 
-    def __init__(self, params, width, n_mid=5, r0=0.6, alpha=0.1, beta=1.1, lam=1.0):
+    def __init__(self, params, width, n_mid=5, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True):
         self.params = np.ascontiguousarray(params, np.float32).ravel()
         self.width, self.n_mid = int(width), int(n_mid)
         self.r0, self.alpha, self.beta = float(r0), float(alpha), float(beta)
+        self.radial = bool(radial)
         n = int(lib().gh_mlp_param_count(self.width, self.n_mid))
         if self.params.size != n:
             raise ValueError("expected %d parameters, got %d" % (n, self.params.size))
-        super().__init__(mlp_blob(self.params, width, n_mid, r0, alpha, beta), lam)
+        super().__init__(mlp_blob(self.params, width, n_mid, r0, alpha, beta, radial), lam)
         self.eps = None
 
     def calibrate(self, N=1024, lo=-1.0, hi=1.0, n_points=1 << 20, seed=0, stream=None) -> float:

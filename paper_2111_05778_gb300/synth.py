@@ -15,6 +15,11 @@ Shapes (the paper's learned SDBs and scenes are not available, Sec. 5):
   each matrix divided by its largest singular value (so g and f are
   1-Lipschitz, i.e. signed distance bounds, Sec. 1) and N(0, 0.01^2) biases.
 * ``batch_items()``: 64 (kind, seed, N, width) items mixing both generators.
+* ``paper_network(seed)``: the paper's own network architecture (Sec. 5.2:
+  3 -> 64, six 64 -> 64, 64 -> 1, ReLU, batch normalisation after every layer
+  but the last) trained with Adam on point-distance samples of a seeded
+  shape (a union of four spheres; the paper's Thingi10K shapes are not
+  available), normalisation folded into the weights; SDB = network / 1.5.
 * ``primitive_scene(seed)``: the seven basic primitives of the paper's first
   scene (Sec. 5.1: sphere, cube, cone, cylinder, torus, hexagonal prism and
   capsule), one of each, randomly rotated, in a union.
@@ -143,6 +148,88 @@ def primitive_scene(seed: int = 0) -> np.ndarray:
             prm = [rng.uniform(0.08, 0.15), rng.uniform(0.06, 0.1)]
         rows.append(prim_row(kind, UNION, c, prm, rot))
     return np.stack(rows)
+
+
+PAPER_WIDTH, PAPER_NMID, PAPER_LAMBDA = 64, 6, 1.5
+
+
+def _blob_shape(rng):
+    """four spheres: centres U[-0.35, 0.35]^3, radii U[0.2, 0.35]"""
+    return rng.uniform(-0.35, 0.35, (4, 3)), rng.uniform(0.2, 0.35, 4)
+
+
+def _blob_distance(C, R, P):
+    # training labels: distance to the union of the spheres (exact outside)
+    return (np.linalg.norm(P[:, None, :] - C[None], axis=2) - R[None]).min(1)
+
+
+def paper_network(seed: int = 0, steps: int = 1500, batch: int = 4096, cache: bool = True):
+    """(params float32 packed like pack_layers, width, n_mid, lambda, (linears,
+    norms)) of the paper's network architecture trained on a seeded shape.
+
+    Samples per step (drawn from the seed): half near the surface (points of
+    the sphere union jittered by N(0, 0.02^2)), half uniform in [-1, 1]^3;
+    labels are distances to the union; L1 loss, Adam (lr 1e-3), batch
+    normalisation in training mode; the running statistics are then folded
+    into the weights (bn.fold_batchnorm).  Trained once per (seed, steps) and
+    cached in the temporary directory."""
+    import os
+    import tempfile
+
+    from .bn import fold_batchnorm
+
+    path = os.path.join(tempfile.gettempdir(), "gh_paper_network_%d_%d_%d.npz" % (seed, steps, batch))
+    if cache and os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        n = int(z["n"])
+        linears = [(z["W%d" % i], z["b%d" % i]) for i in range(n)]
+        norms = [(z["g%d" % i], z["be%d" % i], z["m%d" % i], z["v%d" % i]) if ("g%d" % i) in z else None
+                 for i in range(n)]
+    else:
+        import torch
+
+        rng = np.random.default_rng(seed)
+        C, R = _blob_shape(rng)
+        torch.manual_seed(seed)
+        W = PAPER_WIDTH
+        mods = []
+        dims = [3] + [W] * (PAPER_NMID + 1)
+        for i in range(PAPER_NMID + 1):
+            mods += [torch.nn.Linear(dims[i], W), torch.nn.BatchNorm1d(W), torch.nn.ReLU()]
+        mods.append(torch.nn.Linear(W, 1))
+        net = torch.nn.Sequential(*mods).double()
+        opt = torch.optim.Adam(net.parameters(), lr=1e-3)
+        for _ in range(steps):
+            k = rng.integers(0, 4, batch // 2)
+            d = rng.standard_normal((batch // 2, 3))
+            d /= np.linalg.norm(d, axis=1, keepdims=True)
+            near = C[k] + R[k, None] * d + rng.normal(0.0, 0.02, (batch // 2, 3))
+            P = np.concatenate([near, rng.uniform(-1.0, 1.0, (batch - batch // 2, 3))])
+            y = _blob_distance(C, R, P)
+            pred = net(torch.from_numpy(P))[:, 0]
+            loss = (pred - torch.from_numpy(y)).abs().mean()
+            opt.zero_grad()
+            loss.backward()
+            opt.step()
+        net.eval()
+        lins = [m for m in mods if isinstance(m, torch.nn.Linear)]
+        bns = [m for m in mods if isinstance(m, torch.nn.BatchNorm1d)]
+        linears = [(m.weight.detach().numpy().copy(), m.bias.detach().numpy().copy()) for m in lins]
+        norms = [(b.weight.detach().numpy().copy(), b.bias.detach().numpy().copy(), b.running_mean.numpy().copy(),
+                  b.running_var.numpy().copy()) for b in bns] + [None]
+        if cache:
+            arrs = {"n": np.array(len(linears))}
+            for i, (Wl, bl) in enumerate(linears):
+                arrs["W%d" % i], arrs["b%d" % i] = Wl, bl
+            for i, bn in enumerate(norms):
+                if bn is not None:
+                    arrs["g%d" % i], arrs["be%d" % i], arrs["m%d" % i], arrs["v%d" % i] = bn
+            tmp = path + ".%d.tmp" % os.getpid()
+            np.savez(tmp, **arrs)
+            os.replace(tmp + ".npz" if not tmp.endswith(".npz") else tmp, path)
+    folded = fold_batchnorm(linears, norms)
+    layers = [(Wl.astype(np.float32), bl.astype(np.float32)) for Wl, bl in folded]
+    return pack_layers(layers), PAPER_WIDTH, PAPER_NMID, PAPER_LAMBDA, (linears, norms)
 
 
 def mlp_param_count(width: int, nmid: int = MLP_NMID) -> int:
