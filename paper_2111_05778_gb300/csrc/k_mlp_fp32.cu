@@ -5,7 +5,11 @@
 // 128 points at a time: layer 0 (3 -> W) and the output layer (W -> 1) on
 // CUDA cores directly, the W x W hidden layers as register-blocked FP32
 // products (8 rows x W/16 outputs per thread) whose weights stream from L2
-// through a double-buffered shared-memory ring (cp.async).
+// through a two-buffer shared-memory ring: one thread issues each 32-row
+// chunk as a 1-D bulk copy (cp.async.bulk, mbarrier complete_tx), every warp
+// waits for the chunk on its own, and the last warp to finish reading a
+// buffer issues the chunk two ahead into it -- the warps drift freely inside
+// a layer and meet only around the activation write-back at its end.
 //
 // Two users of the tile engine:
 //   k_hop_mlp_fp32   persistent grid hopper: each of the 128 rows is a ray;
@@ -26,6 +30,8 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
 
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
 template <int W>
 struct Smem {
     float act[W][TM + 4];  // activations, feature-major
@@ -33,36 +39,89 @@ struct Smem {
     float4 p[TM];          // query points
     float g[TM];           // network output
     float red[TM];
+    unsigned long long full[2];  // chunk landed in buffer b (complete_tx)
+    unsigned int done[2];        // warps finished with buffer b
+    int abort;                   // a chunk wait timed out: stop waiting
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
+// waits for the phase of the given parity of buffer b's barrier; after 2 s
+// sets the abort bit (later waits return at once) and the timeout flag
 template <int W>
-__device__ __forceinline__ void issue_chunk(const MlpDev &m, int ch, float *dst) {
+__device__ __noinline__ void wait_chunk(Smem<W> &sm, int b, uint32_t parity, Counters *ctr) {
+    if (mbar_try(&sm.full[b], parity)) return;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(&sm.full[b], parity)) return;
+        if (*(volatile int *)&sm.abort) return;
+        if ((it & 255) == 0 && gtimer() - t0 > WAIT_NS) {
+            atomicOr((int *)&sm.abort, 1);
+            atomicOr(&ctr->flags, FLAG_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// chunk ch of the hidden layers (K rows ch*KC.. of layer ch/NCH) into buffer b
+template <int W>
+__device__ __forceinline__ void issue_chunk(const MlpDev &m, Smem<W> &sm, int ch, int b) {
     constexpr int NCH = W / KC;
+    constexpr uint32_t BYTES = KC * W * 4;
     const int l = ch / NCH, c = ch - l * NCH;
     const float *src = m.wt + (size_t)l * W * W + (size_t)c * KC * W;
-    constexpr int N16 = KC * W / 4;  // float4 count
-    for (int q = threadIdx.x; q < N16; q += NT) cp_async16(dst + 4 * q, src + 4 * q);
-    cp_commit();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&sm.full[b])), "r"(BYTES)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(sm.wbuf[b])),
+                 "l"(src), "r"(BYTES), "r"(su32(&sm.full[b]))
+                 : "memory");
 }
 
-// Evaluates g at sm.p[0..TM) into sm.g.  Must be called by all NT threads.
+// once per CTA, before its first tile
 template <int W>
-__device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
+__device__ __forceinline__ void init_ring(Smem<W> &sm) {
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sm.full[b])) : "memory");
+            sm.done[b] = 0;
+        }
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// Evaluates g at sm.p[0..TM) into sm.g.  Must be called by all NT threads,
+// with both ring buffers free (no chunk in flight).  ph holds the thread's
+// phase bits of the two buffers' barriers across tiles.
+template <int W>
+__device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counters *ctr) {
     constexpr int TO = W / 16;      // outputs per thread
     constexpr int NCH = W / KC;
-    const int tid = threadIdx.x;
-    const int nchunks = m.n_mid * NCH;
-    if (nchunks > 0) issue_chunk<W>(m, 0, sm.wbuf[0]);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nchunks = m.n_mid * NCH;  // >= 2: n_mid >= 1, W / KC >= 2
+    if (tid == 0) {
+        issue_chunk<W>(m, sm, 0, 0);
+        issue_chunk<W>(m, sm, 1, 1);
+    }
     {  // layer 0: 3 -> W on CUDA cores
         const int r = tid & (TM - 1), half = tid >> 7;
         const float4 p = sm.p[r];
@@ -72,6 +131,7 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
             sm.act[o][r] = fmaxf(z, 0.f);
         }
     }
+    __syncthreads();
     // thread (og, rg): rows rg*8 .. rg*8+7, outputs og + 16 j (j < TO); the
     // weight chunk holds, at q*64 + og*4 + e, the weights of output og + 16(4q + e),
     // so each thread reads 16 contiguous bytes and the activation write-back
@@ -86,14 +146,10 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
 #pragma unroll
             for (int p = 0; p < TO / 2; ++p) acc[rr][p] = 0ull;
         for (int c = 0; c < NCH; ++c, ++ch) {
-            if (ch + 1 < nchunks) {
-                issue_chunk<W>(m, ch + 1, sm.wbuf[(ch + 1) & 1]);
-                cp_wait<1>();
-            } else {
-                cp_wait<0>();
-            }
-            __syncthreads();
-            const float *wb = sm.wbuf[ch & 1];
+            const int b = ch & 1;
+            wait_chunk<W>(sm, b, ph[b], ctr);
+            ph[b] ^= 1u;
+            const float *wb = sm.wbuf[b];
 #pragma unroll 4
             for (int kk = 0; kk < KC; ++kk) {
                 const int i = c * KC + kk;
@@ -113,8 +169,15 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
                     }
                 }
             }
-            __syncthreads();
+            // the warp is done with buffer b; the last of the NT/32 warps
+            // refills it with the chunk two ahead
+            __syncwarp();
+            if (lane == 0 && atomicAdd(&sm.done[b], 1u) == NT / 32 - 1) {
+                sm.done[b] = 0;
+                if (ch + 2 < nchunks) issue_chunk<W>(m, sm, ch + 2, b);
+            }
         }
+        __syncthreads();  // every warp has read this layer's input
         // bias + ReLU, back into the activation buffer
         const float *bl = m.bm + (size_t)l * W;
 #pragma unroll
@@ -140,8 +203,8 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm) {
                 *reinterpret_cast<float4 *>(&sm.act[o][rg * 8 + 4]) = v1;
             }
         }
+        __syncthreads();  // the next layer reads this layer's output
     }
-    __syncthreads();
     {  // output layer W -> 1
         const int r = tid & (TM - 1), half = tid >> 7;
         float s = 0.f;
@@ -167,6 +230,8 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
+    init_ring<W>(sm);
+    uint32_t ph[2] = {0u, 0u};
     int cur = 0;
     uint32_t col = NONE, rank = 0;
     int k = 0;
@@ -218,7 +283,7 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
             continue;
         }
         if (tid == 0) atomicAdd(&s.ctr->row_slots, (unsigned long long)TM);
-        mlp_tile<W>(it.m, sm);
+        mlp_tile<W>(it.m, sm, ph, s.ctr);
         if (tid < TM) {
             bool mark = false;
             int step = 1;
@@ -279,6 +344,8 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
     __shared__ unsigned long long tile_s;
     __shared__ unsigned long long total_s;
     const int tid = threadIdx.x;
+    init_ring<W>(sm);
+    uint32_t ph[2] = {0u, 0u};
     for (int cur = 0; cur < n_items;) {
         const Item &it = items[cur];
         const Scratch &s = it.s;
@@ -322,7 +389,7 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
             sm.p[tid] = p;
         }
         __syncthreads();
-        mlp_tile<W>(it.m, sm);
+        mlp_tile<W>(it.m, sm, ph, s.ctr);
         if (tid < TM) {
             const unsigned long long r = t * TM + tid;
             if (r < total) {
