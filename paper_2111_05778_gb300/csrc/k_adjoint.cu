@@ -13,7 +13,8 @@
 //   dL/dW_0 = c sum_v s_v delta_0 p^T,  dL/dw = c sum_v s_v relu(z_L),  dL/db = c sum_v s_v.
 // The activations are recomputed from the vertices (nothing is kept from the
 // polygonization).  Over a chunk of vertices every step is a dense FP32
-// product on the FFMA pipe (k_gemm, 128 x 128 tiles, 8 x 8 per thread); the
+// product on the FFMA pipe (k_gemm, 128 x 128 tiles, 8 x 8 per thread in
+// packed FP32 pairs, register-prefetched 16-deep K slices); the
 // sums over vertices use a split over the vertex axis whose partial results
 // are added in a fixed order, so the gradient is deterministic.
 #include <math.h>
@@ -27,34 +28,35 @@ namespace gh {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, GT = 256;
+constexpr int BM = 128, BN = 128, BK = 16, GT = 256, PADS = 4;
 
 // C[M x N] (+ split z: C + z*M*ldc) = sum_k opA(m,k) opB(k,n) over the k-range
 // [z*kchunk, (z+1)*kchunk) with opA(m,k) = (TA ? A[k*lda+m] : A[m*lda+k]),
 // relu'd if RA and scaled by ksc[k]; opB likewise.  Epilogue: + bias[n],
 // then * [mask[m*ldc+n] > 0].
+// 128 x 128 tile per CTA, 8 x 8 per thread as packed FP32 pairs
+// (fma.rn.f32x2); the next 16-deep K slice is fetched into registers while
+// the current one is multiplied out of the other shared-memory buffer.
 template <bool TA, bool TB, bool RA, bool RB>
 __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *__restrict__ A, int lda,
                                              const float *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
                                              const float *__restrict__ bias, const float *__restrict__ mask,
                                              const float *__restrict__ ksc, int kchunk) {
-    __shared__ __align__(16) float As[BK][BM];
-    __shared__ __align__(16) float Bs[BK][BN];
+    __shared__ __align__(16) float As[2][BK][BM + PADS];
+    __shared__ __align__(16) float Bs[2][BK][BN + PADS];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    float acc[8][8];
+    // each thread stages 8 elements of A and 8 of B per slice: element
+    // e = tid + 256 r (r < 8) of the 128 x 16 slice, walking the contiguous
+    // direction of the operand's storage fastest
+    float ra[8], rb[8];
+    auto fetch = [&](int k0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        // stage 128 x 8 of A and 8 x 128 of B (4 elements per thread each)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int e = tid + r * GT;  // 0..1023
+        for (int r = 0; r < 8; ++r) {
+            const int e = tid + r * GT;  // 0..2047
             {
-                const int mm = TA ? (e & (BM - 1)) : (e >> 3), kk = TA ? (e >> 7) : (e & 7);
+                const int mm = TA ? (e & (BM - 1)) : (e >> 4), kk = TA ? (e >> 7) : (e & (BK - 1));
                 const int m = m0 + mm, k = k0 + kk;
                 float v = 0.f;
                 if (m < M && k < ke) {
@@ -62,35 +64,65 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *_
                     if (RA) v = fmaxf(v, 0.f);
                     if (ksc) v *= ksc[k];
                 }
-                As[kk][mm] = v;
+                ra[r] = v;
             }
             {
-                const int nn = TB ? (e >> 3) : (e & (BN - 1)), kk = TB ? (e & 7) : (e >> 7);
+                const int nn = TB ? (e >> 4) : (e & (BN - 1)), kk = TB ? (e & (BK - 1)) : (e >> 7);
                 const int n = n0 + nn, k = k0 + kk;
                 float v = 0.f;
                 if (n < N && k < ke) {
                     v = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
                     if (RB) v = fmaxf(v, 0.f);
                 }
-                Bs[kk][nn] = v;
+                rb[r] = v;
             }
         }
-        __syncthreads();
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = tid + r * GT;
+            const int mm = TA ? (e & (BM - 1)) : (e >> 4), ka = TA ? (e >> 7) : (e & (BK - 1));
+            const int nn = TB ? (e >> 4) : (e & (BN - 1)), kbb = TB ? (e & (BK - 1)) : (e >> 7);
+            As[buf][ka][mm] = ra[r];
+            Bs[buf][kbb][nn] = rb[r];
+        }
+    };
+    unsigned long long acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
+    int buf = 0;
+    if (kb < ke) {
+        fetch(kb);
+        stash(0);
+    }
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        const bool more = k0 + BK < ke;
+        if (more) fetch(k0 + BK);  // in flight during the products below
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float a[8], b[8];
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 8 + 4]);
-            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8 + 4]);
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(&Bs[buf][kk][tx * 8]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(&Bs[buf][kk][tx * 8 + 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const unsigned long long b[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                unsigned long long a2;
+                asm("mov.b64 %0, {%1, %1};" : "=l"(a2) : "f"(a[i]));
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[i][j]) : "l"(a2), "l"(b[j]));
+            }
         }
-        __syncthreads();
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
     }
     float *Cz = C + (size_t)blockIdx.z * M * ldc;
 #pragma unroll
@@ -98,13 +130,18 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *_
         const int m = m0 + ty * 8 + i;
         if (m >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int n = n0 + tx * 8 + j;
-            if (n >= N) continue;
-            float v = acc[i][j];
-            if (bias) v += bias[n];
-            if (mask && !(mask[(size_t)m * ldc + n] > 0.f)) v = 0.f;
-            Cz[(size_t)m * ldc + n] = v;
+        for (int j = 0; j < 4; ++j) {
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[i][j]));
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int n = n0 + tx * 8 + 2 * j + u;
+                if (n >= N) continue;
+                float v = u ? hi : lo;
+                if (bias) v += bias[n];
+                if (mask && !(mask[(size_t)m * ldc + n] > 0.f)) v = 0.f;
+                Cz[(size_t)m * ldc + n] = v;
+            }
         }
     }
 }
@@ -180,6 +217,42 @@ __global__ void k_adj_reduce(const float *__restrict__ part, int splits, long lo
     }
 }
 
+// part[z][j * NP + a] = sum over rows v of split z (in order) of
+// s[v] * X'[v][j] * P[v][a] (NP = 3) or s[v] * X'[v][j] (NP = 1), with
+// X' = relu(X) if RELU, X' = 1 if X is null.  Column sums of the parameter
+// gradients that have one (or three) outputs per unit: b_l, W_0, w_out.
+template <int NP, bool RELU>
+__global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ X, int V, int W, const float *__restrict__ s,
+                                                const float *__restrict__ P, int rows_per_split,
+                                                float *__restrict__ part) {
+    const int z = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= W) return;
+    const int v0 = z * rows_per_split, v1 = min(V, v0 + rows_per_split);
+    float acc[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) acc[a] = 0.f;
+    for (int v = v0; v < v1; ++v) {
+        float x = X ? X[(size_t)v * W + j] : 1.f;
+        if (RELU) x = fmaxf(x, 0.f);
+        const float sx = s[v] * x;
+        if (NP == 1) {
+            acc[0] += sx;
+        } else {
+#pragma unroll
+            for (int a = 0; a < NP; ++a) acc[a] = fmaf(sx, P[3 * v + a], acc[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) part[(size_t)z * W * NP + (size_t)j * NP + a] = acc[a];
+}
+
+template <int NP, bool RELU>
+void colsum(const float *X, int V, int W, const float *s, const float *P, int splits, float *part, cudaStream_t st) {
+    const int rows = (V + splits - 1) / splits;
+    dim3 grid((W + 255) / 256, splits);
+    k_colsum<NP, RELU><<<grid, 256, 0, st>>>(X, V, W, s, P, rows, part);
+}
+
 __global__ void k_fill(float *p, long long n, float v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = v;
@@ -219,21 +292,21 @@ void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, floa
     const size_t ow = omid + (size_t)L * ((size_t)W * W + W);
     const int gb = 512;
     // W_0 and b_0
-    gemm<true, false, false, false>(W, 3, V, Dl[0], W, P, 3, b.part, 3, nullptr, nullptr, b.s, S, st);
+    colsum<3, false>(Dl[0], V, W, b.s, P, S, b.part, st);
     k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W * 3, c, grad + oW0, accumulate);
-    gemm<true, false, false, false>(W, 1, V, Dl[0], W, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+    colsum<1, false>(Dl[0], V, W, b.s, nullptr, S, b.part, st);
     k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ob0, accumulate);
     for (int l = 1; l <= L; ++l) {
         const size_t oW = omid + (size_t)(l - 1) * ((size_t)W * W + W), ob = oW + (size_t)W * W;
         gemm<true, false, false, true>(W, W, V, Dl[l], W, Zl[l - 1], W, b.part, W, nullptr, nullptr, b.s, S, st);
         k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W * W, c, grad + oW, accumulate);
-        gemm<true, false, false, false>(W, 1, V, Dl[l], W, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+        colsum<1, false>(Dl[l], V, W, b.s, nullptr, S, b.part, st);
         k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ob, accumulate);
     }
-    // output layer
-    gemm<false, false, false, true>(1, W, V, b.ones, V, Zl[L], W, b.part, W, nullptr, nullptr, b.s, S, st);
+    // output layer: w_out from relu(z_L), b_out from the scales alone
+    colsum<1, true>(Zl[L], V, W, b.s, nullptr, S, b.part, st);
     k_adj_reduce<<<gb, 256, 0, st>>>(b.part, S, (long long)W, c, grad + ow, accumulate);
-    gemm<false, false, false, false>(1, 1, V, b.ones, V, b.ones, 1, b.part, 1, nullptr, nullptr, b.s, S, st);
+    colsum<1, false>(nullptr, V, 1, b.s, nullptr, S, b.part, st);
     k_adj_reduce<<<1, 32, 0, st>>>(b.part, S, 1, c, grad + ow + W, accumulate);
 }
 
