@@ -517,7 +517,7 @@ def run_adjoint(args):
     torch.cuda.set_device(0)
     W, N = 256, args.N or 256
     sdb = gh.MlpSdb(synth.mlp_params(1, W), W)
-    verts, faces, _ = gh.unique_vertices(gh.polygonize(sdb, N, keys=True))
+    verts = gh.polygonize(sdb, N, indexed=True).verts  # one vertex per crossing edge, on the device
     c = torch.tensor(np.random.default_rng(4).uniform(-0.05, 0.05, 3), dtype=torch.float32, device="cuda")
     v = verts.clone().requires_grad_(True)
     loss = ((v - c).norm(dim=1) - 0.55).pow(2).mean()

@@ -1079,7 +1079,7 @@ extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL
         return GH_OK;
     }
     std::lock_guard<std::mutex> lk(s->mu);
-    const int W = s->mlp.width, L = s->mlp.n_mid, S = 64;
+    const int W = s->mlp.width, L = s->mlp.n_mid, S = 76;  // 2 x 76 weight-gradient tiles: one per SM
     const int VC = V < 65536 ? (int)V : 65536;
     const size_t need = adjoint_buffer_floats(W, L, 65536, S);
     if (s->adj_floats < need) {
