@@ -296,7 +296,10 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     // FP32 hidden weights: transposed (in-major) with the outputs of a row
     // permuted so that thread group og reads 16 contiguous bytes per step:
     // position q*64 + og*4 + e holds output og + 16*(4q + e).
-    std::vector<float> wt((size_t)h.n_mid * W * W), bm((size_t)h.n_mid * W);
+    // The adjoint's delta chain multiplies by W_l itself (delta_{l-1} = W_l^T
+    // delta_l): wtb holds, per row o of W_l, its inputs i in the same permuted
+    // order (position q*64 + og*4 + e holds input og + 16*(4q + e)).
+    std::vector<float> wt((size_t)h.n_mid * W * W), wtb((size_t)h.n_mid * W * W), bm((size_t)h.n_mid * W);
     const int TO = W / 16;
     for (int l = 0; l < h.n_mid; ++l) {
         const float *Wl = mid + (size_t)l * ((size_t)W * W + W), *bl = Wl + (size_t)W * W;
@@ -306,6 +309,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
                     for (int e = 0; e < 4; ++e) {
                         const int o = og + 16 * (4 * q + e);
                         wt[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)o * W + i];
+                        wtb[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)i * W + o];
                     }
         for (int o = 0; o < W; ++o) bm[(size_t)l * W + o] = bl[o];
     }
@@ -334,9 +338,10 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     std::vector<float> wmid((size_t)h.n_mid * W * W);
     for (int l = 0; l < h.n_mid; ++l)
         memcpy(wmid.data() + (size_t)l * W * W, mid + (size_t)l * ((size_t)W * W + W), sizeof(float) * W * W);
-    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout, *d_wmid;
+    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout, *d_wmid, *d_wtb;
     uint16_t *d_wbf;
     if (dev_alloc(s, &d_w0, 3 * W) || dev_alloc(s, &d_b0, W) || dev_alloc(s, &d_wt, wt.size()) ||
+        dev_alloc(s, &d_wtb, wtb.size()) ||
         dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np) ||
         dev_alloc(s, &d_wbf, wbf.size()) || dev_alloc(s, &d_wmid, wmid.size()))
         return GH_ERR_CUDA;
@@ -345,6 +350,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     GH_CUDA(cudaMemcpy(d_w0, W0, sizeof(float) * 3 * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_b0, B0, sizeof(float) * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
+    GH_CUDA(cudaMemcpy(d_wtb, wtb.data(), sizeof(float) * wtb.size(), cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_bm, bm.data(), sizeof(float) * bm.size(), cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(d_wout, wout, sizeof(float) * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(s->d_params, P, sizeof(float) * np, cudaMemcpyHostToDevice));
@@ -359,6 +365,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.w0 = d_w0;
     m.b0 = d_b0;
     m.wt = d_wt;
+    m.wtb = d_wtb;
     m.bm = d_bm;
     m.wout = d_wout;
     m.bout = wout[W];
@@ -1092,11 +1099,13 @@ extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL
     AdjBuffers b;
     b.VC = 65536;
     b.splits = S;
+    b.nsm = nsm;
     b.Z = s->adj;
     b.D = b.Z + (size_t)(L + 1) * b.VC * W;
     b.s = b.D + (size_t)(L + 1) * b.VC * W;
     b.part = b.s + b.VC;
     b.ones = b.part + (size_t)S * W * W;
+    b.mbits = reinterpret_cast<uint32_t *>(b.ones + b.VC);
     adjoint_fill_ones(b.ones, b.VC, st);
     (void)VC;
     for (long long v0 = 0; v0 < V; v0 += b.VC) {

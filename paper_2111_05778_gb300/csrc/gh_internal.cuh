@@ -63,6 +63,7 @@ struct MlpDev {
     const float *w0;    // [W][3]
     const float *b0;    // [W]
     const float *wt;    // n_mid x [W(in)][W(out)] transposed FP32 hidden weights
+    const float *wtb;   // n_mid x [W(out)][W(in)] FP32 hidden weights, inputs permuted like wt's outputs
     const float *bm;    // n_mid x [W]
     const float *wout;  // [W]
     float bout;
@@ -153,8 +154,16 @@ void launch_index_mesh(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, 
 // implicit-surface adjoint (k_adjoint.cu)
 struct AdjBuffers {
     float *Z, *D, *s, *part, *ones;
-    int VC, splits;
+    uint32_t *mbits;  // ReLU masks of z_0..z_{L-1}: (VC / 128) tiles x 256 threads x W / 64 words per layer
+    int VC, splits, nsm;
 };
+// the adjoint's forward pass (z_0..z_L of V vertices into Z + l*ldl, masks
+// into mbits) and delta chain (delta_L in D + L*ldl down to delta_0),
+// k_mlp_fp32.cu
+void launch_adj_fwd_fp32(const MlpDev &m, const float *P, long long V, float *Z, long long ldl, uint32_t *mbits,
+                         int nsm, cudaStream_t st);
+void launch_adj_bwd_fp32(const MlpDev &m, long long V, const uint32_t *mbits, float *D, long long ldl, int nsm,
+                         cudaStream_t st);
 size_t adjoint_buffer_floats(int W, int n_mid, int VC, int splits);
 void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, float *grad, bool accumulate,
                    const AdjBuffers &b, cudaStream_t st);

@@ -12,9 +12,11 @@
 //   dL/dW_l = c sum_v s_v delta_l relu(z_{l-1})^T,  dL/db_l = c sum_v s_v delta_l,
 //   dL/dW_0 = c sum_v s_v delta_0 p^T,  dL/dw = c sum_v s_v relu(z_L),  dL/db = c sum_v s_v.
 // The activations are recomputed from the vertices (nothing is kept from the
-// polygonization).  Over a chunk of vertices every step is a dense FP32
-// product on the FFMA pipe (k_gemm, 128 x 128 tiles, 8 x 8 per thread in
-// packed FP32 pairs, register-prefetched 16-deep K slices); the
+// polygonization).  Over a chunk of vertices the forward pass (storing every
+// z_l) and the delta chain run on the FP32 tile engine of the network's
+// evaluation (k_mlp_fp32.cu); the weight sums are dense FP32 products on the
+// FFMA pipe (k_gemm, 128 x 128 tiles, 8 x 8 per thread in packed FP32 pairs,
+// register-prefetched 16-deep K slices); the
 // sums over vertices use a split over the vertex axis whose partial results
 // are added in a fixed order, so the gradient is deterministic.
 #include <math.h>
@@ -217,39 +219,54 @@ __global__ void k_adj_reduce(const float *__restrict__ part, int splits, long lo
     }
 }
 
-// part[z][j * NP + a] = sum over rows v of split z (in order) of
-// s[v] * X'[v][j] * P[v][a] (NP = 3) or s[v] * X'[v][j] (NP = 1), with
-// X' = relu(X) if RELU, X' = 1 if X is null.  Column sums of the parameter
-// gradients that have one (or three) outputs per unit: b_l, W_0, w_out.
+// part[z][j * NP + a] = sum over rows v of split z of s[v] * X'[v][j] *
+// P[v][a] (NP = 3) or s[v] * X'[v][j] (NP = 1), with X' = relu(X) if RELU,
+// X' = 1 if X is null.  Column sums of the parameter gradients that have one
+// (or three) outputs per unit: b_l, W_0, w_out.  A block of 32 columns x 8
+// row groups: group g adds the split's rows v = g, g + 8, ... in order, and
+// the 8 group sums are added in group order -- a fixed summation order.
 template <int NP, bool RELU>
 __global__ void __launch_bounds__(256) k_colsum(const float *__restrict__ X, int V, int W, const float *__restrict__ s,
                                                 const float *__restrict__ P, int rows_per_split,
                                                 float *__restrict__ part) {
-    const int z = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= W) return;
+    __shared__ float red[8][32][NP];
+    const int z = blockIdx.y, cx = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + cx;
     const int v0 = z * rows_per_split, v1 = min(V, v0 + rows_per_split);
     float acc[NP];
 #pragma unroll
     for (int a = 0; a < NP; ++a) acc[a] = 0.f;
-    for (int v = v0; v < v1; ++v) {
-        float x = X ? X[(size_t)v * W + j] : 1.f;
-        if (RELU) x = fmaxf(x, 0.f);
-        const float sx = s[v] * x;
-        if (NP == 1) {
-            acc[0] += sx;
-        } else {
+    if (j < W) {
+#pragma unroll 4
+        for (int v = v0 + g; v < v1; v += 8) {
+            float x = X ? X[(size_t)v * W + j] : 1.f;
+            if (RELU) x = fmaxf(x, 0.f);
+            const float sx = s[v] * x;
+            if (NP == 1) {
+                acc[0] += sx;
+            } else {
 #pragma unroll
-            for (int a = 0; a < NP; ++a) acc[a] = fmaf(sx, P[3 * v + a], acc[a]);
+                for (int a = 0; a < NP; ++a) acc[a] = fmaf(sx, P[3 * v + a], acc[a]);
+            }
         }
     }
 #pragma unroll
-    for (int a = 0; a < NP; ++a) part[(size_t)z * W * NP + (size_t)j * NP + a] = acc[a];
+    for (int a = 0; a < NP; ++a) red[g][cx][a] = acc[a];
+    __syncthreads();
+    if (g == 0 && j < W) {
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+            float t = red[0][cx][a];
+            for (int q = 1; q < 8; ++q) t += red[q][cx][a];
+            part[(size_t)z * W * NP + (size_t)j * NP + a] = t;
+        }
+    }
 }
 
 template <int NP, bool RELU>
 void colsum(const float *X, int V, int W, const float *s, const float *P, int splits, float *part, cudaStream_t st) {
     const int rows = (V + splits - 1) / splits;
-    dim3 grid((W + 255) / 256, splits);
+    dim3 grid((W + 31) / 32, splits);
     k_colsum<NP, RELU><<<grid, 256, 0, st>>>(X, V, W, s, P, rows, part);
 }
 
@@ -262,7 +279,8 @@ __global__ void k_fill(float *p, long long n, float v) {
 
 size_t adjoint_buffer_floats(int W, int n_mid, int VC, int splits) {
     const size_t L1 = (size_t)n_mid + 1;
-    return L1 * VC * W * 2 + VC + (size_t)splits * W * W + VC;
+    const size_t mask_words = (size_t)n_mid * ((VC + 127) / 128) * 256 * (W / 64);
+    return L1 * VC * W * 2 + VC + (size_t)splits * W * W + VC + mask_words;
 }
 
 // One chunk of vertices; accumulates into grad (packed like the parameters).
@@ -276,16 +294,12 @@ void adjoint_chunk(const MlpDev &m, const float *P, const float *dL, int V, floa
         Dl[l] = b.D + (size_t)l * b.VC * W;
     }
     const int eb = 1024;
-    // forward: pre-activations of every layer
-    k_adj_in<<<eb, 256, 0, st>>>(P, V, m.w0, m.b0, W, Zl[0]);
-    for (int l = 1; l <= L; ++l)
-        gemm<false, true, true, false>(V, W, W, Zl[l - 1], W, m.wmid + (size_t)(l - 1) * W * W, W, Zl[l], W,
-                                       m.bm + (size_t)(l - 1) * W, nullptr, nullptr, 1, st);
-    // backward chain of g
+    // forward: pre-activations of every layer; backward chain of g (both on the
+    // FP32 tile engine of the network's evaluation)
+    const long long ldl = (long long)b.VC * W;
+    launch_adj_fwd_fp32(m, P, V, b.Z, ldl, b.mbits, b.nsm, st);
     k_adj_top<<<eb, 256, 0, st>>>(Zl[L], V, m.wout, W, Dl[L]);
-    for (int l = L; l >= 1; --l)
-        gemm<false, false, false, false>(V, W, W, Dl[l], W, m.wmid + (size_t)(l - 1) * W * W, W, Dl[l - 1], W,
-                                         nullptr, Zl[l - 1], nullptr, 1, st);
+    launch_adj_bwd_fp32(m, V, b.mbits, b.D, ldl, b.nsm, st);
     k_adj_s<<<(V + 7) / 8, 256, 0, st>>>(P, dL, V, Dl[0], m.w0, W, m.alpha, 1.f / m.beta * m.inv_lam, m.radial, b.s);
     // parameter gradients: sums over the vertices of the chunk
     const size_t oW0 = 0, ob0 = (size_t)3 * W, omid = ob0 + W;

@@ -79,13 +79,22 @@ __device__ __noinline__ void wait_chunk(Smem<W> &sm, int b, uint32_t parity, Cou
     }
 }
 
-// chunk ch of the hidden layers (K rows ch*KC.. of layer ch/NCH) into buffer b
-template <int W>
+// What a tile pass computes: the network value (EVAL), the same with every
+// layer's pre-activation stored (FWDZ, the adjoint's forward pass), or the
+// adjoint's delta chain delta_{l-1} = (W_l^T delta_l) * [z_{l-1} > 0] from
+// delta_L down to delta_0, every delta stored (BACK).
+enum { EVAL = 0, FWDZ = 1, BACK = 2 };
+
+// chunk ch of the hidden layers (K rows ch*KC.. of the pass's ch/NCH-th
+// layer: layer ch/NCH of wt, or for BACK layer n_mid-1-ch/NCH of wtb) into
+// buffer b
+template <int W, int KIND>
 __device__ __forceinline__ void issue_chunk(const MlpDev &m, Smem<W> &sm, int ch, int b) {
     constexpr int NCH = W / KC;
     constexpr uint32_t BYTES = KC * W * 4;
     const int l = ch / NCH, c = ch - l * NCH;
-    const float *src = m.wt + (size_t)l * W * W + (size_t)c * KC * W;
+    const float *src = (KIND == BACK ? m.wtb + (size_t)(m.n_mid - 1 - l) * W * W : m.wt + (size_t)l * W * W) +
+                       (size_t)c * KC * W;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&sm.full[b])), "r"(BYTES)
                  : "memory");
@@ -109,29 +118,55 @@ __device__ __forceinline__ void init_ring(Smem<W> &sm) {
     __syncthreads();
 }
 
-// Evaluates g at sm.p[0..TM) into sm.g.  Must be called by all NT threads,
+// One pass over the tile of TM rows (KIND above).  EVAL: g at sm.p[0..TM)
+// into sm.g.  FWDZ: z_l of rows row0 + r < nrows into zbuf + l*ldl (row-major
+// [row][W]), l = 0..n_mid, and the ReLU masks [z_l > 0] of l < n_mid as bits
+// in the register-tile order of the thread that will apply them (mbits).
+// BACK: sm.act holds delta_{n_mid} (feature-major); delta_{l-1}, masked with
+// those bits, goes to dbuf + (l-1)*ldl.  Must be called by all NT threads,
 // with both ring buffers free (no chunk in flight).  ph holds the thread's
 // phase bits of the two buffers' barriers across tiles.
-template <int W>
-__device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counters *ctr) {
+// Mask words: layer l, tile t, thread tid: mbits[((l * ntiles + t) * NT + tid) * MW + w],
+// bit (j % 4) * 8 + rr of word j / 4 for row rg*8 + rr, output og + 16 j.
+template <int W, int KIND = EVAL>
+__device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counters *ctr, float *zbuf = nullptr,
+                         float *dbuf = nullptr, long long row0 = 0, long long nrows = 0, long long ldl = 0,
+                         uint32_t *mbits = nullptr, long long tile = 0, long long ntiles = 0) {
+    constexpr int MW = W / 64;  // mask words per thread and layer (TO * 8 / 32)
     constexpr int TO = W / 16;      // outputs per thread
     constexpr int NCH = W / KC;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nchunks = m.n_mid * NCH;  // >= 2: n_mid >= 1, W / KC >= 2
     if (tid == 0) {
-        issue_chunk<W>(m, sm, 0, 0);
-        issue_chunk<W>(m, sm, 1, 1);
+        issue_chunk<W, KIND>(m, sm, 0, 0);
+        issue_chunk<W, KIND>(m, sm, 1, 1);
     }
-    {  // layer 0: 3 -> W on CUDA cores
+    if (KIND != BACK) {  // layer 0: 3 -> W on CUDA cores
         const int r = tid & (TM - 1), half = tid >> 7;
         const float4 p = sm.p[r];
+        const bool st = KIND == FWDZ && row0 + r < nrows;
         for (int o = half * (W / 2); o < (half + 1) * (W / 2); ++o) {
             const float z = fmaf(__ldg(m.w0 + 3 * o), p.x,
                                  fmaf(__ldg(m.w0 + 3 * o + 1), p.y, fmaf(__ldg(m.w0 + 3 * o + 2), p.z, __ldg(m.b0 + o))));
             sm.act[o][r] = fmaxf(z, 0.f);
+            if (st) zbuf[(size_t)(row0 + r) * W + o] = z;
+        }
+        __syncthreads();
+        if (KIND == FWDZ) {  // mask bits of z_0 in the register-tile order
+            const int og = tid & 15, rg = tid >> 4;
+            uint32_t wds[MW];
+#pragma unroll
+            for (int w = 0; w < MW; ++w) wds[w] = 0u;
+#pragma unroll
+            for (int j = 0; j < TO; ++j)
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr)
+                    if (sm.act[og + 16 * j][rg * 8 + rr] > 0.f) wds[j >> 2] |= 1u << ((j & 3) * 8 + rr);
+            uint32_t *mp = mbits + ((size_t)tile * NT + tid) * MW;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) mp[w] = wds[w];
         }
     }
-    __syncthreads();
     // thread (og, rg): rows rg*8 .. rg*8+7, outputs og + 16 j (j < TO); the
     // weight chunk holds, at q*64 + og*4 + e, the weights of output og + 16(4q + e),
     // so each thread reads 16 contiguous bytes and the activation write-back
@@ -145,6 +180,12 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counte
         for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
             for (int p = 0; p < TO / 2; ++p) acc[rr][p] = 0ull;
+        uint32_t mw[MW];  // BACK: this thread's mask bits of the layer below, fetched under the products
+        if (KIND == BACK) {
+            const uint32_t *mp = mbits + (((size_t)(m.n_mid - 1 - l) * ntiles + tile) * NT + tid) * MW;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) mw[w] = mp[w];
+        }
         for (int c = 0; c < NCH; ++c, ++ch) {
             const int b = ch & 1;
             wait_chunk<W>(sm, b, ph[b], ctr);
@@ -176,12 +217,18 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counte
             __syncwarp();
             if (lane == 0 && atomicAdd(&sm.done[b], 1u) == NT / 32 - 1) {
                 sm.done[b] = 0;
-                if (ch + 2 < nchunks) issue_chunk<W>(m, sm, ch + 2, b);
+                if (ch + 2 < nchunks) issue_chunk<W, KIND>(m, sm, ch + 2, b);
             }
         }
         __syncthreads();  // every warp has read this layer's input
-        // bias + ReLU, back into the activation buffer
+        // EVAL / FWDZ: bias + ReLU (z stored by FWDZ); BACK: the mask of the
+        // layer below; back into the activation buffer
         const float *bl = m.bm + (size_t)l * W;
+        float *zl = KIND == FWDZ ? zbuf + (size_t)(l + 1) * ldl : nullptr;
+        float *dl = KIND == BACK ? dbuf + (size_t)(m.n_mid - 1 - l) * ldl : nullptr;
+        uint32_t fw[MW];  // FWDZ: mask bits of this layer's z (stored below unless it is the top layer)
+#pragma unroll
+        for (int w = 0; w < MW; ++w) fw[w] = 0u;
 #pragma unroll
         for (int p = 0; p < TO / 2; ++p) {
             float lo[8], hi[8];
@@ -191,23 +238,39 @@ __device__ void mlp_tile(const MlpDev &m, Smem<W> &sm, uint32_t (&ph)[2], Counte
             for (int h = 0; h < 2; ++h) {
                 const float *v = h ? hi : lo;
                 const int o = og + 16 * (2 * p + h);
-                const float b = __ldg(bl + o);
-                float4 v0, v1;
-                v0.x = fmaxf(v[0] + b, 0.f);
-                v0.y = fmaxf(v[1] + b, 0.f);
-                v0.z = fmaxf(v[2] + b, 0.f);
-                v0.w = fmaxf(v[3] + b, 0.f);
-                v1.x = fmaxf(v[4] + b, 0.f);
-                v1.y = fmaxf(v[5] + b, 0.f);
-                v1.z = fmaxf(v[6] + b, 0.f);
-                v1.w = fmaxf(v[7] + b, 0.f);
-                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8]) = v0;
-                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8 + 4]) = v1;
+                float a[8];
+                const int j = 2 * p + h;
+                if (KIND == BACK) {
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) {
+                        const long long row = row0 + rg * 8 + rr;
+                        a[rr] = (mw[j >> 2] >> ((j & 3) * 8 + rr)) & 1u ? v[rr] : 0.f;
+                        if (row < nrows) dl[(size_t)row * W + o] = a[rr];
+                    }
+                } else {
+                    const float b = __ldg(bl + o);
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) {
+                        const float z = v[rr] + b;
+                        a[rr] = fmaxf(z, 0.f);
+                        if (KIND == FWDZ) {
+                            if (row0 + rg * 8 + rr < nrows) zl[(size_t)(row0 + rg * 8 + rr) * W + o] = z;
+                            if (z > 0.f) fw[j >> 2] |= 1u << ((j & 3) * 8 + rr);
+                        }
+                    }
+                }
+                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8]) = make_float4(a[0], a[1], a[2], a[3]);
+                *reinterpret_cast<float4 *>(&sm.act[o][rg * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
             }
+        }
+        if (KIND == FWDZ && l + 1 < m.n_mid) {
+            uint32_t *mp = mbits + (((size_t)(l + 1) * ntiles + tile) * NT + tid) * MW;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) mp[w] = fw[w];
         }
         __syncthreads();  // the next layer reads this layer's output
     }
-    {  // output layer W -> 1
+    if (KIND == EVAL) {  // output layer W -> 1
         const int r = tid & (TM - 1), half = tid >> 7;
         float s = 0.f;
         for (int i = half * (W / 2); i < (half + 1) * (W / 2); ++i) s = fmaf(__ldg(m.wout + i), sm.act[i][r], s);
@@ -407,6 +470,57 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
     }
 }
 
+// The adjoint's forward pass over V vertices P: z_0 .. z_{n_mid} into Z (+ l*ldl).
+template <int W>
+__global__ void __launch_bounds__(NT, 1) k_adj_fwd(MlpDev m, const float *__restrict__ P, long long V,
+                                                   float *__restrict__ Z, long long ldl, uint32_t *__restrict__ mbits,
+                                                   Counters *ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
+    const int tid = threadIdx.x;
+    init_ring<W>(sm);
+    uint32_t ph[2] = {0u, 0u};
+    for (long long t = blockIdx.x; t * TM < V; t += gridDim.x) {
+        const long long row0 = t * TM;
+        if (tid < TM) {
+            const long long r = row0 + tid;
+            sm.p[tid] = r < V ? make_float4(P[3 * r], P[3 * r + 1], P[3 * r + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        mlp_tile<W, FWDZ>(m, sm, ph, ctr, Z, nullptr, row0, V, ldl, mbits, t, (V + TM - 1) / TM);
+    }
+}
+
+// The adjoint's delta chain: delta_{n_mid} from D (+ n_mid*ldl) down to
+// delta_0, masked by the stored pre-activations Z, into D.
+template <int W>
+__global__ void __launch_bounds__(NT, 1) k_adj_bwd(MlpDev m, long long V, const uint32_t *__restrict__ mbits,
+                                                   float *__restrict__ D, long long ldl, Counters *ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
+    const int tid = threadIdx.x;
+    init_ring<W>(sm);
+    uint32_t ph[2] = {0u, 0u};
+    const float *DL = D + (size_t)m.n_mid * ldl;
+    for (long long t = blockIdx.x; t * TM < V; t += gridDim.x) {
+        const long long row0 = t * TM;
+        // delta_L rows into the feature-major buffer, 16 bytes per load
+#pragma unroll 8
+        for (int e = tid; e < TM * W / 4; e += NT) {
+            const int r = e / (W / 4), o = 4 * (e - r * (W / 4));
+            const float4 d = row0 + r < V ? *reinterpret_cast<const float4 *>(DL + (size_t)(row0 + r) * W + o)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            sm.act[o][r] = d.x;
+            sm.act[o + 1][r] = d.y;
+            sm.act[o + 2][r] = d.z;
+            sm.act[o + 3][r] = d.w;
+        }
+        __syncthreads();
+        mlp_tile<W, BACK>(m, sm, ph, ctr, nullptr, D, row0, V, ldl, const_cast<uint32_t *>(mbits), t,
+                          (V + TM - 1) / TM);
+    }
+}
+
 template <class K>
 int occupancy_grid(K kernel, size_t smem, int nsm) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -451,6 +565,39 @@ void launch_lattice_mlp_fp32(const Item *items, int width, int nsm, cudaStream_t
         const size_t smem = sizeof(Smem<WW>);
         const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 3>, smem, nsm);
         k_pts_mlp_fp32<WW, 3><<<grid, NT, smem, st>>>(items, 1, nullptr, 0, nullptr);
+    })
+}
+
+static Counters *adj_counters() {
+    static thread_local Counters *ctr = nullptr;
+    if (!ctr) {
+        cudaMalloc(&ctr, sizeof(Counters));
+        cudaMemset(ctr, 0, sizeof(Counters));
+    }
+    return ctr;
+}
+
+void launch_adj_fwd_fp32(const MlpDev &m, const float *P, long long V, float *Z, long long ldl, uint32_t *mbits,
+                         int nsm, cudaStream_t st) {
+    Counters *ctr = adj_counters();
+    GH_DISPATCH_W(m.width, {
+        const size_t smem = sizeof(Smem<WW>);
+        int grid = occupancy_grid(k_adj_fwd<WW>, smem, nsm);
+        const long long tiles = (V + TM - 1) / TM;
+        if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
+        k_adj_fwd<WW><<<grid, NT, smem, st>>>(m, P, V, Z, ldl, mbits, ctr);
+    })
+}
+
+void launch_adj_bwd_fp32(const MlpDev &m, long long V, const uint32_t *mbits, float *D, long long ldl, int nsm,
+                         cudaStream_t st) {
+    Counters *ctr = adj_counters();
+    GH_DISPATCH_W(m.width, {
+        const size_t smem = sizeof(Smem<WW>);
+        int grid = occupancy_grid(k_adj_bwd<WW>, smem, nsm);
+        const long long tiles = (V + TM - 1) / TM;
+        if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
+        k_adj_bwd<WW><<<grid, NT, smem, st>>>(m, V, mbits, D, ldl, ctr);
     })
 }
 
