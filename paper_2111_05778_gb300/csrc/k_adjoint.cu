@@ -156,16 +156,6 @@ void gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
     k_gemm<TA, TB, RA, RB><<<grid, GT, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ksc, kchunk);
 }
 
-// z_0 = W_0 p + b_0 for a chunk of vertices
-__global__ void k_adj_in(const float *__restrict__ P, int V, const float *__restrict__ w0, const float *__restrict__ b0,
-                         int W, float *__restrict__ Z0) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)V * W;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(e / W), o = (int)(e - (long long)v * W);
-        Z0[e] = fmaf(w0[3 * o], P[3 * v], fmaf(w0[3 * o + 1], P[3 * v + 1], fmaf(w0[3 * o + 2], P[3 * v + 2], b0[o])));
-    }
-}
-
 // delta_L = w * [z_L > 0]
 __global__ void k_adj_top(const float *__restrict__ ZL, int V, const float *__restrict__ wout, int W,
                           float *__restrict__ D) {
