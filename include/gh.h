@@ -209,8 +209,14 @@ typedef struct {
 int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out);
 
 /* Releases an SDB and its device memory.  NULL is accepted.  The caller must
- * make sure no work that uses it is still running. */
+ * make sure no work that uses it is still running.  Its polygonization
+ * scratch (hundreds of MB at N = 1024) is kept in a small per-device pool and
+ * handed to the next SDB that needs no more (no counterpart in the paper;
+ * allocation per object costs milliseconds). */
 int gh_destroy_sdb(gh_sdb *sdb);
+
+/* Frees the pooled scratch of destroyed SDBs on every device.  Always GH_OK. */
+int gh_release_cache(void);
 
 /* Measures the BF16 evaluation error of a neural SDB (the reduced-precision
  * counterpart of the paper's shrink factor lambda, Sec. 5.2): eps = 2 * max

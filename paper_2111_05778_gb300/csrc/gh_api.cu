@@ -228,6 +228,17 @@ struct gh_sdb {
     std::mutex mu;
 };
 
+// Scratch of destroyed SDBs, kept for the next SDB on the same device: the
+// scratch of an N = 1024 polygonization is hundreds of MB, and allocating
+// and freeing it per SDB object costs milliseconds.  gh_release_cache frees it.
+struct PoolEntry {
+    Scratch scr;
+    int N, device;
+};
+static std::mutex g_pool_mu;
+static std::vector<PoolEntry> g_pool;
+constexpr size_t POOL_MAX = 4;
+
 extern "C" int64_t gh_mlp_param_count(int32_t width, int32_t n_mid) {
     const int64_t W = width;
     return 3 * W + W + (int64_t)n_mid * (W * W + W) + W + 1;
@@ -290,70 +301,23 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     const float *P = (const float *)((const char *)d->blob + sizeof(h));
     for (int64_t i = 0; i < np; ++i)
         if (!isfinite(P[i])) return fail(GH_ERR_NONFINITE, "MLP parameter %lld is not finite", (long long)i);
-    const float *W0 = P, *B0 = P + 3 * W;
-    const float *mid = B0 + W;
-    const float *wout = mid + (size_t)h.n_mid * ((size_t)W * W + W);
-    // FP32 hidden weights: transposed (in-major) with the outputs of a row
-    // permuted so that thread group og reads 16 contiguous bytes per step:
-    // position q*64 + og*4 + e holds output og + 16*(4q + e).
-    // The adjoint's delta chain multiplies by W_l itself (delta_{l-1} = W_l^T
-    // delta_l): wtb holds, per row o of W_l, its inputs i in the same permuted
-    // order (position q*64 + og*4 + e holds input og + 16*(4q + e)).
-    std::vector<float> wt((size_t)h.n_mid * W * W), wtb((size_t)h.n_mid * W * W), bm((size_t)h.n_mid * W);
-    const int TO = W / 16;
-    for (int l = 0; l < h.n_mid; ++l) {
-        const float *Wl = mid + (size_t)l * ((size_t)W * W + W), *bl = Wl + (size_t)W * W;
-        for (int i = 0; i < W; ++i)
-            for (int q = 0; q < TO / 4; ++q)
-                for (int og = 0; og < 16; ++og)
-                    for (int e = 0; e < 4; ++e) {
-                        const int o = og + 16 * (4 * q + e);
-                        wt[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)o * W + i];
-                        wtb[(size_t)l * W * W + (size_t)i * W + q * 64 + og * 4 + e] = Wl[(size_t)i * W + o];
-                    }
-        for (int o = 0; o < W; ++o) bm[(size_t)l * W + o] = bl[o];
-    }
-    // BF16 hidden weights for the tensor cores: per layer, K-blocks of 64 inputs;
-    // a K-block holds W rows (outputs) of 128 bytes in the 128-byte swizzled
-    // K-major layout the MMA reads from shared memory: row n, 16-byte chunk c
-    // of inputs [8c, 8c+8) lands at (n/8)*1024 + (n%8)*128 + ((c ^ n%8) * 16).
-    const int KB = W / 64;
-    std::vector<uint16_t> wbf((size_t)h.n_mid * W * W);
-    for (int l = 0; l < h.n_mid; ++l) {
-        const float *Wl = mid + (size_t)l * ((size_t)W * W + W);
-        for (int kb = 0; kb < KB; ++kb) {
-            uint16_t *blk = wbf.data() + ((size_t)l * KB + kb) * (size_t)W * 64;
-            for (int n = 0; n < W; ++n)
-                for (int kk = 0; kk < 64; ++kk) {
-                    const size_t byte = (size_t)(n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7))) << 4) +
-                                        (kk & 7) * 2;
-                    uint32_t u;
-                    const float v = Wl[(size_t)n * W + kb * 64 + kk];
-                    memcpy(&u, &v, 4);
-                    u = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;  // round to nearest even
-                    blk[byte / 2] = (uint16_t)u;
-                }
-        }
-    }
-    std::vector<float> wmid((size_t)h.n_mid * W * W);
-    for (int l = 0; l < h.n_mid; ++l)
-        memcpy(wmid.data() + (size_t)l * W * W, mid + (size_t)l * ((size_t)W * W + W), sizeof(float) * W * W);
-    float *d_w0, *d_b0, *d_wt, *d_bm, *d_wout, *d_wmid, *d_wtb;
+    const float *wout = P + (size_t)4 * W + (size_t)h.n_mid * ((size_t)W * W + W);
+    // the engines' layouts of the hidden weights are derived on the device
+    // (k_prep.cu); layer 0, biases of layer 0 and the output layer are read
+    // in place from the uploaded block
+    const size_t WW = (size_t)W * W;
+    float *d_wt, *d_wtb, *d_bm;
     uint16_t *d_wbf;
-    if (dev_alloc(s, &d_w0, 3 * W) || dev_alloc(s, &d_b0, W) || dev_alloc(s, &d_wt, wt.size()) ||
-        dev_alloc(s, &d_wtb, wtb.size()) ||
-        dev_alloc(s, &d_bm, bm.size()) || dev_alloc(s, &d_wout, W) || dev_alloc(s, &s->d_params, (size_t)np) ||
-        dev_alloc(s, &d_wbf, wbf.size()) || dev_alloc(s, &d_wmid, wmid.size()))
+    if (dev_alloc(s, &s->d_params, (size_t)np) || dev_alloc(s, &d_wt, (size_t)h.n_mid * WW) ||
+        dev_alloc(s, &d_wtb, (size_t)h.n_mid * WW) || dev_alloc(s, &d_bm, (size_t)h.n_mid * W) ||
+        dev_alloc(s, &d_wbf, (size_t)h.n_mid * WW))
         return GH_ERR_CUDA;
-    GH_CUDA(cudaMemcpy(d_wmid, wmid.data(), sizeof(float) * wmid.size(), cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_wbf, wbf.data(), sizeof(uint16_t) * wbf.size(), cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_w0, W0, sizeof(float) * 3 * W, cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_b0, B0, sizeof(float) * W, cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_wtb, wtb.data(), sizeof(float) * wtb.size(), cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_bm, bm.data(), sizeof(float) * bm.size(), cudaMemcpyHostToDevice));
-    GH_CUDA(cudaMemcpy(d_wout, wout, sizeof(float) * W, cudaMemcpyHostToDevice));
     GH_CUDA(cudaMemcpy(s->d_params, P, sizeof(float) * np, cudaMemcpyHostToDevice));
+    launch_prep_mlp(s->d_params, W, h.n_mid, d_wt, d_wtb, d_wbf, d_bm, 0);
+    GH_CUDA(cudaGetLastError());
+    GH_CUDA(cudaStreamSynchronize(0));  // the layouts are complete before any stream uses them
+    const float *d_w0 = s->d_params, *d_b0 = s->d_params + 3 * W;
+    const float *d_wout = s->d_params + (size_t)4 * W + (size_t)h.n_mid * (WW + W);
     MlpDev &m = s->mlp;
     m.width = W;
     m.n_mid = h.n_mid;
@@ -370,8 +334,24 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.wout = d_wout;
     m.bout = wout[W];
     m.wbf = d_wbf;
-    m.wmid = d_wmid;
     s->nparam = np;
+    return GH_OK;
+}
+
+extern "C" int gh_release_cache(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (PoolEntry &e : g_pool) {
+        cudaSetDevice(e.device);
+        Scratch &c = e.scr;
+        void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
+                        c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+    g_pool.clear();
+    cudaSetDevice(cur);
     return GH_OK;
 }
 
@@ -413,6 +393,14 @@ static void free_scratch(gh_sdb *s) {
 
 extern "C" int gh_destroy_sdb(gh_sdb *s) {
     if (!s) return GH_OK;
+    if (s->scr.ctr) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (g_pool.size() < POOL_MAX) {
+            g_pool.push_back(PoolEntry{s->scr, s->scr_N, s->device});
+            s->scr = Scratch{};
+            s->scr_N = 0;
+        }
+    }
     free_scratch(s);
     if (s->adj) cudaFree(s->adj);
     if (s->d_item) cudaFree(s->d_item);
@@ -421,9 +409,23 @@ extern "C" int gh_destroy_sdb(gh_sdb *s) {
     return GH_OK;
 }
 
-// Allocates the scratch of an N-grid with at least the given capacities.
+// Allocates the scratch of an N-grid with at least the given capacities (a
+// fresh SDB first takes an adequate one from the pool).
 static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want_verts) {
     Scratch &c = s->scr;
+    if (!c.ctr) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        for (size_t q = 0; q < g_pool.size(); ++q) {
+            const PoolEntry &e = g_pool[q];
+            if (e.device == s->device && e.N >= N && e.scr.cap_marks >= want_marks && e.scr.cap_verts >= want_verts) {
+                c = e.scr;
+                s->scr_N = e.N;
+                s->item_valid = false;
+                g_pool.erase(g_pool.begin() + (long)q);
+                break;
+            }
+        }
+    }
     const bool grid_ok = s->scr_N >= N;
     if (grid_ok && c.cap_marks >= want_marks && c.cap_verts >= want_verts) return GH_OK;
     const int NN = grid_ok ? s->scr_N : N;

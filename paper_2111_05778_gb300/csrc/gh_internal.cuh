@@ -68,7 +68,6 @@ struct MlpDev {
     const float *wout;  // [W]
     float bout;
     const uint16_t *wbf;  // n_mid x BF16 hidden weights in the tensor-core tile layout
-    const float *wmid;    // n_mid x [W(out)][W(in)] FP32 hidden weights, row-major
 };
 
 // Scratch of one polygonization (device pointers) and its capacities.
@@ -148,6 +147,9 @@ void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);  // k_pi
 void scan_u32_dev(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
                   Counters *ctr, cudaStream_t st);
 long long scan_partials(long long n);
+// derived weight layouts of a neural SDB from its packed parameters (k_prep.cu)
+void launch_prep_mlp(const float *params, int W, int n_mid, float *wt, float *wtb, uint16_t *wbf, float *bm,
+                     cudaStream_t st);
 // indexed mesh output after Marching Cubes (k_index.cu)
 void launch_index_mesh(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
 

@@ -107,6 +107,7 @@ def lib():
                 "gh_polygonize_csg_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), P, I32, I32,
                                                              ctypes.POINTER(MeshDesc), P]),
                 "gh_last_profile": (ctypes.c_int, [ctypes.POINTER(Profile)]),
+                "gh_release_cache": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -121,7 +122,7 @@ def exported_symbols():
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
             "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc", "gh_batch_graph_launch",
-            "gh_batch_graph_free"]
+            "gh_batch_graph_free", "gh_release_cache"]
 
 
 def check(rc):
@@ -496,6 +497,11 @@ def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):
     check(lib().gh_eval(sdb.handle, p.data_ptr(), p.shape[0], out.data_ptr(), PRECISIONS[precision],
                         _stream_ptr(stream)))
     return out
+
+
+def release_cache():
+    """Frees the scratch the library keeps from destroyed SDBs (gh_release_cache)."""
+    check(lib().gh_release_cache())
 
 
 def set_profiling(enable: bool):
