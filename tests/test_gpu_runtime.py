@@ -29,7 +29,9 @@ def test_pooled_scratch_gives_identical_meshes():
     b = gh.MlpSdb(p, 128)  # takes it
     m = gh.polygonize(b, 160, keys=True)
     assert (_canon(m) == ref_t).all()
-    assert m.stats == ref.stats
+    # every count but row_slots (tile steps: depends on the dynamic column claims)
+    strip = lambda st: {k: v for k, v in st.items() if k != "row_slots"}
+    assert strip(m.stats) == strip(ref.stats)
     b.close()
     # an analytic SDB on a smaller grid reuses the same buffers
     prims = synth.csg_prims(4)
