@@ -63,6 +63,26 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_replicas(total_ms, units, steps, world, device="cpu"):
+    """Whole-job throughput of `world` independent replicas (weak scaling:
+    each rank polygonizes its own mesh): the slowest rank's time (max over
+    ranks of the timed region) and the units of all ranks.  Returns
+    (ms per step, units per second).  Needs an initialised process group when
+    world > 1 (NCCL on GPUs, gloo in the CPU tests)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([float(total_ms), float(units)], dtype=torch.float64, device=device)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        total_ms, units = float(mx[0].item()), float(tot[1].item())
+    ms = total_ms / steps
+    return ms, units / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # oracle on the host cores (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
@@ -234,13 +254,8 @@ def run_ours(args):
     total_ms = float(sum(step_ms))
     st = bufs.stats_dict()
     assert st["status"] == 0, st
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms = total_ms / args.steps
     cells = st["surface_cells"]
-    value = cells * world / (ms / 1e3)
+    ms, value = aggregate_replicas(total_ms, cells, args.steps, world, device=dev)
 
     # rooflines of the kernels that dominate the step, from the phase events
     peaks, peak_kind = measured_peaks()
