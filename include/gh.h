@@ -57,7 +57,12 @@ extern "C" {
  * f = op_{n-1}( ... op_1(d_0, d_1) ..., d_{n-1}) -- a left fold where union is
  * min (Sec. 4.3), subtract is max(f, -d) and intersect is max(f, d).  Every
  * primitive is an exact Euclidean distance, so f is a signed distance bound
- * (Sec. 1).  q = rot * (p - centre) is the point in the primitive's frame. */
+ * (Sec. 1).  q = rot * (p - centre) is the point in the primitive's frame;
+ * rot must be a rotation (|rot rot^T - I| <= 1e-4 entrywise, else
+ * gh_create_sdb returns GH_ERR_ARG), and spheres do not read it.  The
+ * evaluator skips a primitive whose distance provably cannot change the fold
+ * (bounding-ball test, exact: the result equals the full fold bit for bit);
+ * that test is only taken for positive sizes and |rot rot^T - I| <= 1e-6. */
 #define GH_PRIM_SPHERE 0 /* param[0] = radius                                 */
 #define GH_PRIM_TORUS 1  /* around local y: param[0] = major R, param[1] = r   */
 #define GH_PRIM_BOX 2    /* exact box distance (Sec. 4.2), half sizes param[] */
@@ -83,7 +88,7 @@ typedef struct {
     float centre[3];
     float param[3];
     float rot[9]; /* row-major, world offset -> local frame */
-    float pad[3];
+    float pad[3];  /* ignored (the library's copy keeps the bounding radius there) */
 } gh_csg_prim; /* 80 bytes */
 
 /* MLP blob (the neural SDB of Sec. 5.2, Eq. 7): gh_mlp_header followed by
@@ -271,7 +276,9 @@ int gh_batch_graph_free(void *graph);
  * library keeps from load until the process exits.
  *   grid:   as in gh_polygonize, with N <= GH_NOALLOC_MAX_N.
  *   prims:  device array of n_prim gh_csg_prim records (1 <= n_prim <=
- *           GH_MAX_PRIMS); caller-owned, only read.
+ *           GH_MAX_PRIMS); caller-owned, only read (a copy with bounding
+ *           radii is staged in the static array).  They must meet the rules
+ *           gh_create_sdb checks; being on the device, they are not checked.
  *   out:    caller-owned device buffers, as in gh_polygonize.
  *   stream: a cudaStream_t (NULL = legacy default stream).
  * The call waits for its stream and reports errors as gh_polygonize with

@@ -272,6 +272,17 @@ static int create_csg(gh_sdb *s, const gh_sdb_desc *d) {
             if (!isfinite(p.centre[q]) || !isfinite(p.param[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite", i);
         for (int q = 0; q < 9; ++q)
             if (!isfinite(p.rot[q])) return fail(GH_ERR_ARG, "primitive %d: non-finite rotation", i);
+        // a rotation keeps the primitive's distance a distance (1-Lipschitz,
+        // as hopping requires); a scaled or sheared matrix does not
+        double dev = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double e = r == c ? -1.0 : 0.0;
+                for (int k = 0; k < 3; ++k) e += (double)p.rot[3 * r + k] * (double)p.rot[3 * c + k];
+                dev = fmax(dev, fabs(e));
+            }
+        if (dev > 1e-4)
+            return fail(GH_ERR_ARG, "primitive %d: rotation is not orthonormal (|R R^T - I| = %.3g)", i, dev);
         if (p.type == GH_PRIM_CONE && !(p.param[0] > 0.f && p.param[1] > 0.f))
             return fail(GH_ERR_ARG, "primitive %d: cone needs R > 0 and H > 0", i);
         // the shrink factor lambda of Sec. 5.2 applies to analytic SDBs as a
@@ -280,6 +291,14 @@ static int create_csg(gh_sdb *s, const gh_sdb_desc *d) {
         // only accepted as 1 for CSG.
     }
     if (s->lam != 1.f) return fail(GH_ERR_UNIMPLEMENTED, "lipschitz_scale != 1 is supported for neural SDBs only");
+    // pad[0] of the device copy holds the primitive's bounding radius, which
+    // lets the evaluator skip primitives that cannot change the fold
+    for (gh_csg_prim &p : pr) {
+        Prim q;
+        memcpy(&q, &p, sizeof(q));
+        p.pad[0] = prim_bound_radius(q);
+        p.pad[1] = p.pad[2] = 0.f;
+    }
     if (dev_alloc(s, &s->d_prims, pr.size())) return GH_ERR_CUDA;
     GH_CUDA(cudaMemcpy(s->d_prims, pr.data(), pr.size() * sizeof(gh_csg_prim), cudaMemcpyHostToDevice));
     s->nprim = h.n_prim;
@@ -1172,6 +1191,8 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     Scratch c{};
     c.ctr = (Counters *)(q + off);
     off += up256(sizeof(Counters));
+    Prim *staged = (Prim *)(q + off);  // the caller's records with their bounding radii
+    off += up256(sizeof(Prim) * GH_MAX_PRIMS);
     c.colcount = (uint32_t *)(q + off);
     off += up256(4 * ncols);
     c.coloff = (uint32_t *)(q + off);
@@ -1196,7 +1217,7 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     c.cap_verts = (long long)(2 * M);
     if (off > GH_NOALLOC_SCRATCH_BYTES) return fail(GH_ERR_CUDA, "no-allocation scratch layout overflows");
     cudaStream_t st = (cudaStream_t)stream;
-    const Prim *dp = reinterpret_cast<const Prim *>(prims);
+    const Prim *dp = staged;
     Item hitem{};
     hitem.g = g;
     hitem.s = c;
@@ -1205,6 +1226,7 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     hitem.kind = GH_SDB_CSG;
     GH_CUDA(cudaMemcpyAsync(ditem, &hitem, sizeof(Item), cudaMemcpyHostToDevice, st));
     launch_init(c, st);  // clears the counters left by the previous call
+    launch_stage_prims(reinterpret_cast<const Prim *>(prims), staged, n_prim, st);
     launch_hop_csg(ditem, 1, n_prim, nsm, 256, st);
     launch_build_lists(g, c, st);
     launch_eval_vertices_csg(dp, n_prim, g, c, nsm, st);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/gh.h"
@@ -54,6 +55,38 @@ struct Prim {
     float pad[3];
 };
 static_assert(sizeof(Prim) == 80, "Prim layout");
+
+// Bounding radius rb of a primitive: the largest distance from its centre to
+// a point of the solid, rounded up.  For an exact distance d of a solid
+// inside the ball B(c, rb), |p - c| - rb <= d(p) <= |p - c| + rb; the CSG
+// evaluator uses the interval to skip primitives that cannot change the
+// min / max fold.  The bound is only claimed for the shapes it was derived
+// for: positive sizes and an orthonormal rotation (|R R^T - I| <= 1e-6
+// entrywise); any other record gets +inf, which turns the skip off.
+__host__ __device__ inline float prim_bound_radius(const Prim &q) {
+    const double a = q.p[0], b = q.p[1], c = q.p[2];
+    double e = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = i == j ? -1.0 : 0.0;
+            for (int k = 0; k < 3; ++k) s += (double)q.rot[3 * i + k] * (double)q.rot[3 * j + k];
+            e = s > e ? s : (-s > e ? -s : e);
+        }
+    const bool box = q.type == GH_PRIM_BOX;
+    const bool pos = a > 0.0 && (q.type == GH_PRIM_SPHERE || b > 0.0) && (!box || c > 0.0);
+    if (!(e <= 1e-6) || !pos) return INFINITY;
+    double rb;
+    switch (q.type) {
+    case GH_PRIM_SPHERE: rb = a; break;
+    case GH_PRIM_TORUS: rb = a + b; break;                        // major + minor radius
+    case GH_PRIM_BOX: rb = sqrt(a * a + b * b + c * c); break;    // corner
+    case GH_PRIM_CAPSULE: rb = a + b; break;                      // half length + radius
+    case GH_PRIM_CYLINDER: rb = sqrt(a * a + b * b); break;       // rim (radius, half height)
+    case GH_PRIM_HEXPRISM: rb = sqrt(4.0 * a * a / 3.0 + b * b); break;  // corner: circumradius 2a / sqrt(3)
+    default: rb = sqrt(a * a + b * b); break;                     // cone: base rim (R, -H)
+    }
+    return (float)(rb * (1.0 + 1e-6)) + 1e-6f;
+}
 
 // Neural SDB parameters on the device.
 struct MlpDev {
@@ -114,6 +147,7 @@ __host__ __device__ inline uint32_t mark_rank(unsigned long long m) { return (ui
 // ---- launchers implemented in the kernels' translation units ----------------
 cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges);  // k_pipeline.cu
 void launch_init(Scratch &s, cudaStream_t st);
+void launch_stage_prims(const Prim *src, Prim *dst, int nprim, cudaStream_t st);  // records + bounding radii
 void launch_hop_csg(const Item *items, int n_items, int max_prims, int nsm, int block, cudaStream_t st);
 void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,

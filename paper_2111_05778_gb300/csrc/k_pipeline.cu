@@ -119,11 +119,30 @@ __device__ __forceinline__ float prim_dist(const float4 *q, float x, float y, fl
     }
 }
 
+// The left fold of Sec. 4.3.  A primitive's distance d lies in
+// [|p - c| - rb, |p - c| + rb] (rb: its bounding radius, record slot 18): the
+// solid lies in the ball B(c, rb), and d is 1-Lipschitz with |d(c)| <= rb.
+// When that interval (widened by a margin far above FP32 rounding) shows that
+// min(f, d), max(f, -d) or max(f, d) would return f, the exact distance is
+// not evaluated: f is bit-for-bit what the full fold gives.  Spheres are
+// always evaluated (their bound costs as much as their distance).
 __device__ __forceinline__ float csg_eval(const float4 *P, int n, float x, float y, float z) {
     int op;
     float f = prim_dist(P, x, y, z, op);
     for (int i = 1; i < n; ++i) {
-        const float d = prim_dist(P + 5 * i, x, y, z, op);
+        const float4 *q = P + 5 * i;
+        const float4 a = q[0], b = q[1];
+        const int type = __float_as_int(a.x);
+        op = __float_as_int(a.y);
+        if (type != GH_PRIM_SPHERE) {
+            const float dx = x - a.z, dy = y - a.w, dz = z - b.x;
+            const float dc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), rb = q[4].y;
+            const float m = 2e-5f * (dc + rb + fabsf(f) + 1.f);
+            const bool skip = op == GH_OP_UNION ? dc - rb >= f + m
+                                                : (op == GH_OP_SUBTRACT ? dc - rb >= m - f : dc + rb + m <= f);
+            if (skip) continue;
+        }
+        const float d = prim_dist(q, x, y, z, op);
         f = op == GH_OP_UNION ? fminf(f, d) : (op == GH_OP_SUBTRACT ? fmaxf(f, -d) : fmaxf(f, d));
     }
     return f;
@@ -135,6 +154,21 @@ __device__ __forceinline__ void load_prims(float4 *dst, const Prim *src, int npr
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
     for (int i = threadIdx.x; i < nprim * 5; i += blockDim.x) dst[i] = s4[i];
     __syncthreads();
+}
+
+// Copy caller-owned primitive records and write each one's bounding radius
+// into pad[0] (the slot the evaluator reads it from); pad[1..2] are cleared.
+__global__ void k_stage_prims(const Prim *__restrict__ src, Prim *__restrict__ dst, int nprim) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nprim) return;
+    Prim q = src[i];
+    q.pad[0] = prim_bound_radius(q);
+    q.pad[1] = q.pad[2] = 0.f;
+    dst[i] = q;
+}
+
+void launch_stage_prims(const Prim *src, Prim *dst, int nprim, cudaStream_t st) {
+    k_stage_prims<<<(nprim + 127) / 128, 128, 0, st>>>(src, dst, nprim);
 }
 
 // ---------------------------------------------------------------------------

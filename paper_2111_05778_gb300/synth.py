@@ -150,6 +150,26 @@ def primitive_scene(seed: int = 0) -> np.ndarray:
     return np.stack(rows)
 
 
+def mixed_prims(seed: int, n: int = 96) -> np.ndarray:
+    """Many-primitive CSG scene of all seven kinds: draw order per primitive
+    kind U{0..6}, centre U[-0.7,0.7]^3, rotation from a normalised 4-D
+    Gaussian quaternion, sizes U[0.04,0.16] (a, b, c in the kind's parameter
+    order), op union (first primitive, then with probability 0.8) else
+    subtract; the fold ends with an intersection with a box of half sizes
+    U[0.6,0.8]^3 at the origin."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        kind = int(rng.integers(0, 7))
+        c = rng.uniform(-0.7, 0.7, 3)
+        rot = _quat_rot(rng.standard_normal(4))
+        prm = rng.uniform(0.04, 0.16, 3)
+        op = UNION if i == 0 or rng.uniform() < 0.8 else SUBTRACT
+        rows.append(prim_row(kind, op, c, prm if kind == BOX else prm[:2], rot))
+    rows.append(prim_row(BOX, INTERSECT, np.zeros(3), rng.uniform(0.6, 0.8, 3), _quat_rot(rng.standard_normal(4))))
+    return np.stack(rows)
+
+
 PAPER_WIDTH, PAPER_NMID, PAPER_LAMBDA = 64, 6, 1.5
 
 

@@ -33,7 +33,8 @@ def _check_same(bufs, ref, N, lo, hi):
 
 
 def test_noalloc_matches_polygonize_on_two_calls():
-    cases = [(synth.csg_prims(0), 128, -1.0, 1.0), (synth.sphere_prims(0.5), 200, -0.8, 0.8)]
+    cases = [(synth.csg_prims(0), 128, -1.0, 1.0), (synth.sphere_prims(0.5), 200, -0.8, 0.8),
+             (synth.mixed_prims(7), 150, -1.0, 1.0)]
     for prims, N, lo, hi in cases:
         ref = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True)
         bufs = gh.Buffers(ref.n_tris + 100, keys=True)
