@@ -50,6 +50,18 @@ static constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_
 // with min / max (Sec. 4.2-4.3).  Primitives are read from shared memory as
 // five float4 each (all lanes read the same primitive: broadcast).
 // ---------------------------------------------------------------------------
+// Square root on the special-function unit (PTX sqrt.approx.f32, one
+// instruction instead of the correctly rounded sequence).  Its error is a
+// few units in the last place, far inside the evaluation error budget that
+// the results are checked against; every GPU consumer of an analytic SDB
+// (hopper, vertex values, point evaluation, enumeration lattice) calls the
+// same evaluator, so they agree bit for bit.
+__device__ __forceinline__ float fsqrt(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // 2-D signed distance to the regular hexagon of apothem a with edges facing
 // 0, 60, ..., 300 degrees: fold into the wedge [-30, 30] degrees, where the
 // nearest edge is x = a, |z| <= a / sqrt(3).
@@ -64,26 +76,26 @@ __device__ __forceinline__ float hexagon2(float x, float z, float a) {
     }
     const float lim = a * 0.5773502691896258f;
     const float v0 = x - a, v1 = z - fminf(fmaxf(z, -lim), lim);
-    const float n = sqrtf(fmaf(v0, v0, v1 * v1));
+    const float n = fsqrt(fmaf(v0, v0, v1 * v1));
     return v0 < 0.f ? -n : n;
 }
 
 // (radius, height) box combination used by the cylinder and the prism
 __device__ __forceinline__ float box2(float e0, float e1) {
     const float o0 = fmaxf(e0, 0.f), o1 = fmaxf(e1, 0.f);
-    return sqrtf(fmaf(o0, o0, o1 * o1)) + fminf(fmaxf(e0, e1), 0.f);
+    return fsqrt(fmaf(o0, o0, o1 * o1)) + fminf(fmaxf(e0, e1), 0.f);
 }
 
 // solid cone, base disc radius R at y = -H, apex at +H; 2-D in (rho, y)
 __device__ __forceinline__ float cone2(float rho, float y, float R, float H) {
     const float bs = fminf(fmaxf(rho, 0.f), R);
     const float b0 = rho - bs, b1 = y + H;
-    const float db = sqrtf(fmaf(b0, b0, b1 * b1));
+    const float db = fsqrt(fmaf(b0, b0, b1 * b1));
     const float e0 = -R, e1 = 2.f * H;
     float t = fmaf(rho - R, e0, (y + H) * e1) / fmaf(e0, e0, e1 * e1);
     t = fminf(fmaxf(t, 0.f), 1.f);
     const float s0 = rho - fmaf(t, e0, R), s1 = y - fmaf(t, e1, -H);
-    const float d = fminf(db, sqrtf(fmaf(s0, s0, s1 * s1)));
+    const float d = fminf(db, fsqrt(fmaf(s0, s0, s1 * s1)));
     const bool inside = y > -H && y < H && rho * 2.f * H < R * (H - y);
     return inside ? -d : d;
 }
@@ -94,27 +106,27 @@ __device__ __forceinline__ float prim_dist(const float4 *q, float x, float y, fl
     const int type = __float_as_int(a.x);
     op = __float_as_int(a.y);
     const float dx = x - a.z, dy = y - a.w, dz = z - b.x;
-    if (type == GH_PRIM_SPHERE) return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - b.y;
+    if (type == GH_PRIM_SPHERE) return fsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - b.y;
     const float4 r0 = q[2], r1 = q[3], r2 = q[4];  // rot[0..3], rot[4..7], rot[8], pad
     const float lx = fmaf(r0.x, dx, fmaf(r0.y, dy, r0.z * dz));
     const float ly = fmaf(r0.w, dx, fmaf(r1.x, dy, r1.y * dz));
     const float lz = fmaf(r1.z, dx, fmaf(r1.w, dy, r2.x * dz));
     switch (type) {
     case GH_PRIM_TORUS: {
-        const float t = sqrtf(fmaf(lx, lx, lz * lz)) - b.y;
-        return sqrtf(fmaf(t, t, ly * ly)) - b.z;
+        const float t = fsqrt(fmaf(lx, lx, lz * lz)) - b.y;
+        return fsqrt(fmaf(t, t, ly * ly)) - b.z;
     }
     case GH_PRIM_CAPSULE: {
         const float v1 = ly - fminf(fmaxf(ly, -b.y), b.y);
-        return sqrtf(fmaf(lx, lx, fmaf(v1, v1, lz * lz))) - b.z;
+        return fsqrt(fmaf(lx, lx, fmaf(v1, v1, lz * lz))) - b.z;
     }
-    case GH_PRIM_CYLINDER: return box2(sqrtf(fmaf(lx, lx, lz * lz)) - b.y, fabsf(ly) - b.z);
+    case GH_PRIM_CYLINDER: return box2(fsqrt(fmaf(lx, lx, lz * lz)) - b.y, fabsf(ly) - b.z);
     case GH_PRIM_HEXPRISM: return box2(hexagon2(lx, lz, b.y), fabsf(ly) - b.z);
-    case GH_PRIM_CONE: return cone2(sqrtf(fmaf(lx, lx, lz * lz)), ly, b.y, b.z);
+    case GH_PRIM_CONE: return cone2(fsqrt(fmaf(lx, lx, lz * lz)), ly, b.y, b.z);
     default: {
         const float ex = fabsf(lx) - b.y, ey = fabsf(ly) - b.z, ez = fabsf(lz) - b.w;
         const float ox = fmaxf(ex, 0.f), oy = fmaxf(ey, 0.f), oz = fmaxf(ez, 0.f);
-        return sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(fmaxf(ex, fmaxf(ey, ez)), 0.f);
+        return fsqrt(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(fmaxf(ex, fmaxf(ey, ez)), 0.f);
     }
     }
 }
@@ -136,7 +148,7 @@ __device__ __forceinline__ float csg_eval(const float4 *P, int n, float x, float
         op = __float_as_int(a.y);
         if (type != GH_PRIM_SPHERE) {
             const float dx = x - a.z, dy = y - a.w, dz = z - b.x;
-            const float dc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), rb = q[4].y;
+            const float dc = fsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), rb = q[4].y;
             const float m = 2e-5f * (dc + rb + fabsf(f) + 1.f);
             const bool skip = op == GH_OP_UNION ? dc - rb >= f + m
                                                 : (op == GH_OP_SUBTRACT ? dc - rb >= m - f : dc + rb + m <= f);
