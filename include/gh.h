@@ -88,7 +88,7 @@ typedef struct {
     float centre[3];
     float param[3];
     float rot[9]; /* row-major, world offset -> local frame */
-    float pad[3];  /* ignored (the library's copy keeps the bounding radius there) */
+    float pad[3];  /* ignored (the library's copy keeps derived data there) */
 } gh_csg_prim; /* 80 bytes */
 
 /* MLP blob (the neural SDB of Sec. 5.2, Eq. 7): gh_mlp_header followed by

@@ -291,13 +291,16 @@ static int create_csg(gh_sdb *s, const gh_sdb_desc *d) {
         // only accepted as 1 for CSG.
     }
     if (s->lam != 1.f) return fail(GH_ERR_UNIMPLEMENTED, "lipschitz_scale != 1 is supported for neural SDBs only");
-    // pad[0] of the device copy holds the primitive's bounding radius, which
-    // lets the evaluator skip primitives that cannot change the fold
-    for (gh_csg_prim &p : pr) {
-        Prim q;
-        memcpy(&q, &p, sizeof(q));
-        p.pad[0] = prim_bound_radius(q);
-        p.pad[1] = p.pad[2] = 0.f;
+    // the device copy keeps derived data in the spare slots: pad[0] the
+    // primitive's bounding radius (the evaluator skips primitives that cannot
+    // change the fold), pad[1] the length of the union-sphere run it starts
+    std::vector<Prim> q(pr.size());
+    memcpy(q.data(), pr.data(), pr.size() * sizeof(Prim));
+    for (size_t i = 0; i < pr.size(); ++i) {
+        const int run = prim_sphere_run(q.data(), (int)q.size(), (int)i);
+        pr[i].pad[0] = prim_bound_radius(q[i]);
+        memcpy(&pr[i].pad[1], &run, sizeof(run));
+        pr[i].pad[2] = 0.f;
     }
     if (dev_alloc(s, &s->d_prims, pr.size())) return GH_ERR_CUDA;
     GH_CUDA(cudaMemcpy(s->d_prims, pr.data(), pr.size() * sizeof(gh_csg_prim), cudaMemcpyHostToDevice));

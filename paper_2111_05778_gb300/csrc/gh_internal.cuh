@@ -88,6 +88,16 @@ __host__ __device__ inline float prim_bound_radius(const Prim &q) {
     return (float)(rb * (1.0 + 1e-6)) + 1e-6f;
 }
 
+// Length of the run of spheres starting at record i that the CSG fold
+// combines by min (record 0's op is never used, later records must be
+// unions); 0 when record i starts no such run.  The evaluator takes a run's
+// minimum in one tight loop (min is exact, so the fold's value is unchanged).
+__host__ __device__ inline int prim_sphere_run(const Prim *p, int n, int i) {
+    int k = i;
+    while (k < n && p[k].type == GH_PRIM_SPHERE && (k == 0 || p[k].op == GH_OP_UNION)) ++k;
+    return k - i;
+}
+
 // Neural SDB parameters on the device.
 struct MlpDev {
     int width, n_mid;

@@ -132,17 +132,44 @@ __device__ __forceinline__ float prim_dist(const float4 *q, float x, float y, fl
 }
 
 // The left fold of Sec. 4.3.  A primitive's distance d lies in
-// [|p - c| - rb, |p - c| + rb] (rb: its bounding radius, record slot 18): the
+// [|p - c| - rb, |p - c| + rb] (rb: its bounding radius, record slot 17): the
 // solid lies in the ball B(c, rb), and d is 1-Lipschitz with |d(c)| <= rb.
 // When that interval (widened by a margin far above FP32 rounding) shows that
 // min(f, d), max(f, -d) or max(f, d) would return f, the exact distance is
 // not evaluated: f is bit-for-bit what the full fold gives.  Spheres are
-// always evaluated (their bound costs as much as their distance).
+// always evaluated (their bound costs as much as their distance); a run of
+// spheres joined by union (its length in record slot 18) is folded as the
+// minimum of the run, in a loop without the per-primitive dispatch.
+__device__ __forceinline__ float sphere_run_min(const float4 *P, int i0, int cnt, float x, float y, float z) {
+    float m = INFINITY;
+#pragma unroll 4
+    for (int j = i0; j < i0 + cnt; ++j) {
+        const float4 a = P[5 * j], b = P[5 * j + 1];  // type, op, cx, cy | cz, r, -, -
+        const float dx = x - a.z, dy = y - a.w, dz = z - b.x;
+        m = fminf(m, fsqrt(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - b.y);
+    }
+    return m;
+}
+
 __device__ __forceinline__ float csg_eval(const float4 *P, int n, float x, float y, float z) {
-    int op;
-    float f = prim_dist(P, x, y, z, op);
-    for (int i = 1; i < n; ++i) {
+    int op, i;
+    float f;
+    const int run0 = __float_as_int(P[4].z);
+    if (run0 >= 2) {
+        f = sphere_run_min(P, 0, run0, x, y, z);
+        i = run0;
+    } else {
+        f = prim_dist(P, x, y, z, op);
+        i = 1;
+    }
+    for (; i < n; ++i) {
         const float4 *q = P + 5 * i;
+        const int run = __float_as_int(q[4].z);
+        if (run >= 2) {
+            f = fminf(f, sphere_run_min(P, i, run, x, y, z));
+            i += run - 1;
+            continue;
+        }
         const float4 a = q[0], b = q[1];
         const int type = __float_as_int(a.x);
         op = __float_as_int(a.y);
@@ -168,14 +195,16 @@ __device__ __forceinline__ void load_prims(float4 *dst, const Prim *src, int npr
     __syncthreads();
 }
 
-// Copy caller-owned primitive records and write each one's bounding radius
-// into pad[0] (the slot the evaluator reads it from); pad[1..2] are cleared.
+// Copy caller-owned primitive records and write the derived slots the
+// evaluator reads: pad[0] the bounding radius, pad[1] the union-sphere run
+// length; pad[2] is cleared.
 __global__ void k_stage_prims(const Prim *__restrict__ src, Prim *__restrict__ dst, int nprim) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nprim) return;
     Prim q = src[i];
     q.pad[0] = prim_bound_radius(q);
-    q.pad[1] = q.pad[2] = 0.f;
+    q.pad[1] = __int_as_float(prim_sphere_run(src, nprim, i));
+    q.pad[2] = 0.f;
     dst[i] = q;
 }
 
