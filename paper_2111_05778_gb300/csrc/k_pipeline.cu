@@ -10,10 +10,10 @@
 //                     after a warp ballot; marks are appended with one atomic
 //                     per warp.
 //   2. scans + k_scatter_marks   group the marks by column (k ascending).
-//   3. k_lines        for every vertical lattice line, merge the marks of the
-//                     (up to) four adjacent columns into the sorted set of
-//                     lattice vertices the marked cells need, so each vertex
-//                     is evaluated once.
+//   3. k_lines        for every vertical lattice line, collect the marks of
+//                     the (up to) four adjacent columns into the ascending
+//                     set of lattice vertices the marked cells need, so each
+//                     vertex is evaluated once.
 //   4. k_eval_vertices_csg   f at those vertices.
 //   5. k_mc           per marked cell: 8 corner values, case index, table
 //                     lookup, edge interpolation, warp prefix-sum emit with one
@@ -432,54 +432,68 @@ __global__ void k_scatter_marks(Scratch s) {
 // ---------------------------------------------------------------------------
 // 3. Lattice lines.  Line (a,b), 0 <= a,b <= N, holds the lattice vertices
 //    (a,b,c).  A marked cell (i,j,k) needs c = k and c = k+1 on the lines
-//    (i,j), (i+1,j), (i,j+1), (i+1,j+1).  Merging the k-sorted mark lists of
-//    the four columns around a line gives its vertices in ascending c.
+//    (i,j), (i+1,j), (i,j+1), (i+1,j+1).  Each thread gathers the vertices of
+//    one line as a bit set over c = 0..N in shared memory (its own words,
+//    interleaved with the other threads' so that equal word indices hit
+//    different banks), reading the mark lists of the four columns around the
+//    line with independent loads; pass 1 counts the set bits, pass 2 writes
+//    the keys in ascending c.
 // ---------------------------------------------------------------------------
+constexpr int LINES_T = 128;
+
+__device__ __forceinline__ void set_cells(uint32_t *bits, uint32_t k) {
+    bits[(k >> 5) * LINES_T] |= 1u << (k & 31);
+    const uint32_t k1 = k + 1;  // k + 1 <= N
+    bits[(k1 >> 5) * LINES_T] |= 1u << (k1 & 31);
+}
+
 template <bool EMIT>
-__global__ void k_lines(GridP g, Scratch s) {
+__global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
+    extern __shared__ uint32_t lbits[];
     if (s.ctr->flags & STOP_FLAGS) return;
-    const int N = g.N, N1 = N + 1;
+    const int N = g.N, N1 = N + 1, NW = (N1 + 31) >> 5;
+    uint32_t *bits = lbits + threadIdx.x;  // word w at bits[w * LINES_T]
+    const unsigned long long *__restrict__ mk = s.marks_csr;
+    const uint32_t *__restrict__ off = s.coloff;
     const long long nlines = (long long)N1 * N1;
     const unsigned long long cap = (unsigned long long)s.cap_verts;
     for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
          line += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(line / N1), b = (int)(line - (long long)a * N1);
-        uint32_t beg[4], end[4];
-        int nl = 0;
+        for (int w = 0; w < NW; ++w) bits[w * LINES_T] = 0u;
         for (int di = -1; di <= 0; ++di)
             for (int dj = -1; dj <= 0; ++dj) {
                 const int i = a + di, j = b + dj;
                 if (i < 0 || j < 0 || i >= N || j >= N) continue;
                 const uint32_t col = (uint32_t)i * N + j;
-                beg[nl] = s.coloff[col];
-                end[nl] = s.coloff[col + 1];
-                ++nl;
+                uint32_t m = off[col];
+                const uint32_t e = off[col + 1];
+                for (; m + 4 <= e; m += 4) {
+                    const unsigned long long r0 = __ldg(mk + m), r1 = __ldg(mk + m + 1), r2 = __ldg(mk + m + 2),
+                                             r3 = __ldg(mk + m + 3);
+                    set_cells(bits, mark_k(r0));
+                    set_cells(bits, mark_k(r1));
+                    set_cells(bits, mark_k(r2));
+                    set_cells(bits, mark_k(r3));
+                }
+                for (; m < e; ++m) set_cells(bits, mark_k(__ldg(mk + m)));
             }
-        uint32_t head[4];
-        for (int q = 0; q < nl; ++q) head[q] = beg[q] < end[q] ? mark_k(s.marks_csr[beg[q]]) : NONE;
-        int last = -1;
-        uint32_t cnt = 0;
-        const unsigned long long obase = EMIT ? s.lineoff[line] : 0ull;
-        for (;;) {
-            int best = -1;
-            uint32_t bk = NONE;
-            for (int q = 0; q < nl; ++q)
-                if (head[q] < bk) {
-                    bk = head[q];
-                    best = q;
+        if (!EMIT) {
+            uint32_t cnt = 0;
+            for (int w = 0; w < NW; ++w) cnt += (uint32_t)__popc(bits[w * LINES_T]);
+            s.linecount[line] = cnt;
+        } else {
+            unsigned long long o = s.lineoff[line];
+            for (int w = 0; w < NW; ++w) {
+                uint32_t v = bits[w * LINES_T];
+                while (v) {
+                    const int bit = __ffs(v) - 1;
+                    v &= v - 1;
+                    if (o < cap) s.vkey[o] = (unsigned long long)line | ((unsigned long long)(32 * w + bit) << 32);
+                    ++o;
                 }
-            if (best < 0) break;
-            ++beg[best];
-            head[best] = beg[best] < end[best] ? mark_k(s.marks_csr[beg[best]]) : NONE;
-            for (int c = (int)bk; c <= (int)bk + 1; ++c)
-                if (c > last) {
-                    if (EMIT && obase + cnt < cap)
-                        s.vkey[obase + cnt] = (unsigned long long)line | ((unsigned long long)c << 32);
-                    ++cnt;
-                    last = c;
-                }
+            }
         }
-        if (!EMIT) s.linecount[line] = cnt;
     }
 }
 
@@ -491,11 +505,12 @@ void launch_build_lists(const GridP &g, Scratch &s, cudaStream_t st) {
     const long long ncols = (long long)g.N * g.N, nlines = (long long)(g.N + 1) * (g.N + 1);
     scan_u32(s.colcount, ncols, s.coloff, s.blocksum, nullptr, s.ctr, st);
     k_scatter_marks<<<1024, 256, 0, st>>>(s);
-    const int lb = (int)((nlines + 255) / 256);
-    k_lines<false><<<lb, 256, 0, st>>>(g, s);
+    const int lb = (int)((nlines + LINES_T - 1) / LINES_T);
+    const size_t lsm = (size_t)((g.N + 1 + 31) / 32) * LINES_T * sizeof(uint32_t);  // <= 33 KB at N = 2048
+    k_lines<false><<<lb, LINES_T, lsm, st>>>(g, s);
     scan_u32(s.linecount, nlines, s.lineoff, s.blocksum, &s.ctr->verts, s.ctr, st);
     k_check_verts<<<1, 1, 0, st>>>(s);
-    k_lines<true><<<lb, 256, 0, st>>>(g, s);
+    k_lines<true><<<lb, LINES_T, lsm, st>>>(g, s);
 }
 
 // ---------------------------------------------------------------------------
