@@ -157,7 +157,10 @@ typedef struct {
     int64_t columns;         /* N^2                                           */
     int64_t hop_evals;       /* f evaluations made by the rays                */
     int64_t marked_cells;    /* cells within tau                              */
-    int64_t unique_vertices; /* lattice vertices evaluated for Marching Cubes */
+    int64_t unique_vertices; /* lattice vertices evaluated for Marching Cubes:
+                                the corners of marked cells except those whose
+                                hop value |f| - eps exceeds sqrt(3)/2 h + eps
+                                (plus a rounding margin), which hold no zero */
     int64_t refined_vertices;/* of those, re-evaluated in FP32 (BF16 path)    */
     int64_t surface_cells;   /* marked cells with 0 < case < 255              */
     int64_t triangles;       /* triangles produced (may exceed capacity)      */

@@ -146,9 +146,22 @@ struct Item {
     int kind;
 };
 
-// Packing of mark records.
-__host__ __device__ inline unsigned long long pack_mark(uint32_t col, uint32_t k, uint32_t rank) {
-    return (unsigned long long)col | ((unsigned long long)k << 24) | ((unsigned long long)rank << 40);
+// Packing of mark records.  MARK_EMPTY: the hop value proves that the cell
+// holds no zero of f and that all its corner values have one certain sign,
+// so the cell is kept in the marked set (it was reached within tau) but its
+// corners are not evaluated and Marching Cubes skips it.
+constexpr unsigned long long MARK_EMPTY = 1ull << 63;
+__host__ __device__ inline unsigned long long pack_mark(uint32_t col, uint32_t k, uint32_t rank, bool empty) {
+    return (unsigned long long)col | ((unsigned long long)k << 24) | ((unsigned long long)rank << 40) |
+           (empty ? MARK_EMPTY : 0ull);
+}
+__host__ __device__ inline bool mark_empty(unsigned long long m) { return (m & MARK_EMPTY) != 0ull; }
+// d = |f(centre)| - eps at a marked cell centre (x, y, z).  With f
+// 1-Lipschitz, |f| >= d - sqrt(3)/2 h at every point of the cell, so when d
+// exceeds sqrt(3)/2 h + eps + an FP32 rounding margin the cell has no zero and
+// every corner value (BF16 within eps, or FP32) has the sign of f.
+__host__ __device__ inline bool cell_is_empty(const GridP &g, float d, float x, float y, float z) {
+    return d > 0.8660254f * g.h + g.eps + 1e-5f * (1.f + fabsf(x) + fabsf(y) + fabsf(z));
 }
 __host__ __device__ inline uint32_t mark_col(unsigned long long m) { return (uint32_t)(m & 0xFFFFFFull); }
 __host__ __device__ inline uint32_t mark_k(unsigned long long m) { return (uint32_t)((m >> 24) & 0xFFFFull); }

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             // 4. f, then the hop step or the store
             const float f = outer_f(m, px, py, pz, gsum + m.bout);
             if (MODE == MODE_HOP) {
-                bool mark = false;
+                bool mark = false, empty = false;
                 int step = 1;
                 if (live) {
                     float d = fabsf(f) - g.eps;
@@ -595,6 +595,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     }
                     if (d <= g.tau) {
                         mark = true;
+                        empty = cell_is_empty(g, d, px, py, pz);
                     } else {
                         const float stp = floorf(d * g.inv_h);
                         step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     if (lane == leader) pend_base = atomicAdd(&ctr->marks, (unsigned long long)__popc(mm));
                     pend_mark = true;
                     pend_mask = mm;
-                    if (mark) pend_rec = pack_mark(col, (uint32_t)k, rank);
+                    if (mark) pend_rec = pack_mark(col, (uint32_t)k, rank, empty);
                 }
                 if (live) {
                     if (mark) {

@@ -350,10 +350,11 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
         if (tid == 0) atomicAdd(&s.ctr->row_slots, (unsigned long long)TM);
         mlp_tile<W>(it.m, sm, ph, s.ctr);
         if (tid < TM) {
-            bool mark = false;
+            bool mark = false, empty = false;
             int step = 1;
             if (live) {
-                const float f = outer_f(it.m, sm.p[tid], sm.g[tid]);
+                const float4 pc = sm.p[tid];
+                const float f = outer_f(it.m, pc, sm.g[tid]);
                 ++evals;
                 float d = fabsf(f) - g.eps;
                 if (!isfinite(f)) {
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
                 }
                 if (d <= g.tau) {
                     mark = true;
+                    empty = cell_is_empty(g, d, pc.x, pc.y, pc.z);
                 } else {
                     const float stp = floorf(d * g.inv_h);
                     step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
                 if (mark) {
                     const unsigned long long idx = base + __popc(mm & lt);
                     if (idx < (unsigned long long)s.cap_marks)
-                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
+                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank, empty);
                     else
                         atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
                 }

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(512) k_hop_csg(const Item *__restrict__ items,
             }
             const bool live = col != NONE;
             if (!__any_sync(FULL, live)) break;
-            bool mark = false;
+            bool mark = false, empty = false;
             int step = 1;
             if (live) {
                 const float z = fmaf((float)k + 0.5f, g.h, g.lo[2]);
@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(512) k_hop_csg(const Item *__restrict__ items,
                 }
                 if (d <= g.tau) {
                     mark = true;
+                    empty = cell_is_empty(g, d, x, y, z);
                 } else {
                     const float stp = floorf(d * g.inv_h);
                     step = stp < 1.f ? 1 : (stp > (float)N ? N : (int)stp);
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(512) k_hop_csg(const Item *__restrict__ items,
                 if (mark) {
                     const unsigned long long idx = base + __popc(mm & lt);
                     if (idx < (unsigned long long)s.cap_marks)
-                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank);
+                        s.marks_raw[idx] = pack_mark(col, (uint32_t)k, rank, empty);
                     else
                         atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
                 }
@@ -425,7 +426,7 @@ __global__ void k_scatter_marks(Scratch s) {
          m += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long r = s.marks_raw[m];
         const uint32_t col = mark_col(r);
-        s.marks_csr[s.coloff[col] + mark_rank(r)] = r & 0xFFFFFFFFFFull;
+        s.marks_csr[s.coloff[col] + mark_rank(r)] = r & (0xFFFFFFFFFFull | MARK_EMPTY);
     }
 }
 
@@ -441,7 +442,10 @@ __global__ void k_scatter_marks(Scratch s) {
 // ---------------------------------------------------------------------------
 constexpr int LINES_T = 128;
 
-__device__ __forceinline__ void set_cells(uint32_t *bits, uint32_t k) {
+// the corners c = k, k + 1 of a marked cell (none for a cell marked empty)
+__device__ __forceinline__ void set_cells(uint32_t *bits, unsigned long long r) {
+    if (mark_empty(r)) return;
+    const uint32_t k = mark_k(r);
     bits[(k >> 5) * LINES_T] |= 1u << (k & 31);
     const uint32_t k1 = k + 1;  // k + 1 <= N
     bits[(k1 >> 5) * LINES_T] |= 1u << (k1 & 31);
@@ -471,12 +475,12 @@ __global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
                 for (; m + 4 <= e; m += 4) {
                     const unsigned long long r0 = __ldg(mk + m), r1 = __ldg(mk + m + 1), r2 = __ldg(mk + m + 2),
                                              r3 = __ldg(mk + m + 3);
-                    set_cells(bits, mark_k(r0));
-                    set_cells(bits, mark_k(r1));
-                    set_cells(bits, mark_k(r2));
-                    set_cells(bits, mark_k(r3));
+                    set_cells(bits, r0);
+                    set_cells(bits, r1);
+                    set_cells(bits, r2);
+                    set_cells(bits, r3);
                 }
-                for (; m < e; ++m) set_cells(bits, mark_k(__ldg(mk + m)));
+                for (; m < e; ++m) set_cells(bits, __ldg(mk + m));
             }
         if (!EMIT) {
             uint32_t cnt = 0;
@@ -671,11 +675,11 @@ __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
     for (unsigned long long m0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); m0 < M;
          m0 += stride) {
         const unsigned long long m = m0 + lane;
-        const bool valid = m < M;
+        const unsigned long long r = m < M ? s.marks_csr[m] : MARK_EMPTY;
+        const bool valid = !mark_empty(r);  // cells marked empty have no triangles
         float fv[8];
         int i = 0, j = 0, k = 0;
         if (valid) {
-            const unsigned long long r = s.marks_csr[m];
             const uint32_t col = mark_col(r);
             k = (int)mark_k(r);
             i = (int)(col / (uint32_t)N);
@@ -781,6 +785,7 @@ __global__ void k_refine_select(GridP g, Scratch s) {
     for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
          m += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long r = s.marks_csr[m];
+        if (mark_empty(r)) continue;  // no corners evaluated, no crossing edge
         const uint32_t col = mark_col(r), k = mark_k(r);
         const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
         uint32_t vi[8];
