@@ -46,7 +46,8 @@ template <int W>
 struct SmemB {
     uint8_t a[2][W / 64][TM * 128];  // A operands: one per tile, K-blocks of 128 rows x 128 B (1024-aligned)
     uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
-    float4 w0b[2][W];                // per tile: layer-0 rows and biases of its current item
+    float4 w0b[2][W];                // per tile: layer-0 rows and biases of its current item, by output
+                                     // pairs (2p, 2p+1): {wx, wx', wy, wy'}, {wz, wz', b, b'}
     float bmid[2][MAXMID * W];       // per tile: hidden-layer biases
     float wout[2][W];                // per tile: output-layer weights
     unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2], a_full[2], item_ready[2], drain;
@@ -157,6 +158,17 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
         : "memory");
 }
 
+// packed FP32 pairs (fma.rn.f32x2: two independent IEEE fused multiply-adds)
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -214,7 +226,11 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         const MlpDev &m0 = items[0].m;
         for (int i = tid; i < TILES * W; i += blockDim.x) {
             const int t = i / W, o = i - t * W;
-            sm.w0b[t][o] = make_float4(m0.w0[3 * o], m0.w0[3 * o + 1], m0.w0[3 * o + 2], m0.b0[o]);
+            float *q = reinterpret_cast<float *>(&sm.w0b[t][o & ~1]) + (o & 1);
+            q[0] = m0.w0[3 * o];
+            q[2] = m0.w0[3 * o + 1];
+            q[4] = m0.w0[3 * o + 2];
+            q[6] = m0.b0[o];
             sm.wout[t][o] = m0.wout[o];
         }
         for (int i = tid; i < TILES * n_mid * W; i += blockDim.x) {
@@ -480,7 +496,11 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 {
                     const MlpDev &mm = it->m;
                     for (int o = row; o < W; o += 128) {
-                        w0b[o] = make_float4(mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+                        float *q = reinterpret_cast<float *>(&w0b[o & ~1]) + (o & 1);
+                        q[0] = mm.w0[3 * o];
+                        q[2] = mm.w0[3 * o + 1];
+                        q[4] = mm.w0[3 * o + 2];
+                        q[6] = mm.b0[o];
                         wout[o] = mm.wout[o];
                     }
                     for (int i = row; i < n_mid * W; i += 128) bmid[i] = mm.bm[i];
@@ -496,15 +516,19 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             const MlpDev &m = it->m;
             // 2. layer 0 (FP32) -> A operand (two 8-output groups per iteration
             // so that the loads of one overlap the FMAs of the other)
+            const unsigned long long ppx = pack2(px, px), ppy = pack2(py, py), ppz = pack2(pz, pz);
 #pragma unroll 2
             for (int o = 0; o < W; o += 8) {
                 uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float4 w0 = w0b[o + 2 * e], w1 = w0b[o + 2 * e + 1];
-                    const float z0 = fmaf(w0.x, px, fmaf(w0.y, py, fmaf(w0.z, pz, w0.w)));
-                    const float z1 = fmaf(w1.x, px, fmaf(w1.y, py, fmaf(w1.z, pz, w1.w)));
-                    pk[e] = pack_relu_bf16(z0, z1);
+                    // outputs o + 2e and o + 2e + 1 as one packed pair: the same
+                    // fused multiply-adds, in the same order, as the scalar form
+                    const float4 wa = w0b[o + 2 * e], wb = w0b[o + 2 * e + 1];
+                    const unsigned long long z = ffma2(pack2(wa.x, wa.y), ppx,
+                                                       ffma2(pack2(wa.z, wa.w), ppy,
+                                                             ffma2(pack2(wb.x, wb.y), ppz, pack2(wb.z, wb.w))));
+                    pk[e] = pack_relu_bf16(lo2(z), hi2(z));
                 }
                 const int kb = o >> 6, c = (o & 63) >> 3;
                 sts128(arow + kb * (TM * 128) + ((c ^ sw) << 4), pk[0], pk[1], pk[2], pk[3]);
