@@ -279,8 +279,8 @@ int gh_batch_graph_free(void *graph);
  * library keeps from load until the process exits.
  *   grid:   as in gh_polygonize, with N <= GH_NOALLOC_MAX_N.
  *   prims:  device array of n_prim gh_csg_prim records (1 <= n_prim <=
- *           GH_MAX_PRIMS); caller-owned, only read (a copy with bounding
- *           radii is staged in the static array).  They must meet the rules
+ *           GH_MAX_PRIMS); caller-owned, only read (a copy with derived
+ *           data is staged in the static array).  They must meet the rules
  *           gh_create_sdb checks; being on the device, they are not checked.
  *   out:    caller-owned device buffers, as in gh_polygonize.
  *   stream: a cudaStream_t (NULL = legacy default stream).
