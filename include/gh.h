@@ -313,7 +313,12 @@ int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int
  *   are not differentiated).  Each vertex contributes to the one primitive the
  *   min/max fold selects there.
  * dL_dtheta is device float32 and is overwritten.  Deterministic
- * (fixed-order reductions).  V = 0 gives zeros. */
+ * (fixed-order reductions).  V = 0 gives zeros.  Neural SDBs take the
+ * vertices in chunks of GH_ADJOINT_CHUNK (the SDB keeps a work buffer of
+ * 2 (n_mid + 1) width floats per chunk vertex); the result is the sum of the
+ * chunks' gradients in chunk order, so it equals, bit for bit, the sum of
+ * separate calls on those chunks. */
+#define GH_ADJOINT_CHUNK 131072
 int gh_backward(const gh_sdb *sdb, const float *verts, const float *dL_dv, int64_t V, float *dL_dtheta,
                 void *stream);
 

@@ -1111,8 +1111,10 @@ extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL
     }
     std::lock_guard<std::mutex> lk(s->mu);
     const int W = s->mlp.width, L = s->mlp.n_mid, S = 76;  // 2 x 76 weight-gradient tiles: one per SM
-    const int VC = V < 65536 ? (int)V : 65536;
-    const size_t need = adjoint_buffer_floats(W, L, 65536, S);
+    // vertices per chunk: the stored activations and deltas of a chunk take
+    // 2 (L + 1) W floats per vertex (1.6 GB at W = 256, L = 5)
+    constexpr int VCHUNK = GH_ADJOINT_CHUNK;
+    const size_t need = adjoint_buffer_floats(W, L, VCHUNK, S);
     if (s->adj_floats < need) {
         if (s->adj) cudaFree(s->adj);
         s->adj = nullptr;
@@ -1121,7 +1123,7 @@ extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL
         s->adj_floats = need;
     }
     AdjBuffers b;
-    b.VC = 65536;
+    b.VC = VCHUNK;
     b.splits = S;
     b.nsm = nsm;
     b.Z = s->adj;
@@ -1131,7 +1133,6 @@ extern "C" int gh_backward(const gh_sdb *cs, const float *verts, const float *dL
     b.ones = b.part + (size_t)S * W * W;
     b.mbits = reinterpret_cast<uint32_t *>(b.ones + b.VC);
     adjoint_fill_ones(b.ones, b.VC, st);
-    (void)VC;
     for (long long v0 = 0; v0 < V; v0 += b.VC) {
         const int n = (int)((V - v0) < b.VC ? (V - v0) : b.VC);
         adjoint_chunk(s->mlp, verts + 3 * v0, dL_dv + 3 * v0, n, dL_dtheta, v0 > 0, b, st);

@@ -434,6 +434,7 @@ def polygonize_batch(sdbs, Ns, lo=-1.0, hi=1.0, precision="fp32", keys=False, ep
 
 
 NOALLOC_MAX_N = 256
+ADJOINT_CHUNK = 131072  # GH_ADJOINT_CHUNK: vertices per chunk of gh_backward
 
 
 def csg_prims_device(prims, device=None):

@@ -72,20 +72,22 @@ def test_adjoint_matches_oracle_and_finite_differences():
 
 
 def test_adjoint_is_deterministic_and_chunked():
-    """Bit-identical on repeat; a call over 150001 vertices (three chunks of
-    the vertex axis) equals the sum of the calls on each chunk exactly; and it
+    """Bit-identical on repeat; a call over 2 chunks + 1 vertices (three
+    chunks of the vertex axis) equals the sum of the calls on each chunk
+    exactly; and it
     matches the FP64 oracle.  With random-sign dL/dv the sums cancel heavily,
     so a few components whose vertices sit on a ReLU kink within FP32
     rounding differ from FP64 by more than 1e-3: at least 99 % agree."""
     sdb = gh.MlpSdb(synth.mlp_params(2, 64), 64)
     rng = np.random.default_rng(0)
-    n = 150001
+    C = gh.ADJOINT_CHUNK
+    n = 2 * C + 1
     V = torch.from_numpy(rng.uniform(-0.7, 0.7, (n, 3)).astype(np.float32)).cuda()
     G = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).cuda()
     a = gh.backward(sdb, V, G)
     b = gh.backward(sdb, V, G)
     assert torch.equal(a, b)
-    parts = [gh.backward(sdb, V[s:e], G[s:e]) for s, e in ((0, 65536), (65536, 131072), (131072, n))]
+    parts = [gh.backward(sdb, V[s:e], G[s:e]) for s, e in ((0, C), (C, 2 * C), (2 * C, n))]
     assert torch.equal(a, (parts[0] + parts[1]) + parts[2])
     ref = oracle.np_adjoint(sdb.params.astype(np.float64), 64, 5, V.cpu().numpy(), G.cpu().numpy())
     assert _rel_ok(a.cpu().numpy().astype(np.float64), ref).mean() > 0.99
