@@ -18,8 +18,9 @@
  *   Sec. 4.1   plane distance (Eq. 5); Sec. 4.2 box distance (Eq. 6) and the
  *              exact box distance; Sec. 4.3 union of shapes by min.
  *   Sec. 2     enumeration: Marching Cubes on every one of the N^3 cells.
- *   Sec. 5     "all implementations produce exactly the same meshes";
- *              Sec. 5.2 the neural SDB (Eq. 7) shrunk by lambda.
+ *   Sec. 5     every method compared there yields the identical mesh (the
+ *              invariant the tests check); Sec. 5.2 the neural SDB (Eq. 7)
+ *              shrunk by lambda.
  *
  * Conventions (the paper's unit cube generalised to [lo, lo + N h]^3):
  *   cell (i,j,k) = [lo+ih, lo+(i+1)h] x ... ; its centre lo + (i+1/2)h ...
