@@ -77,8 +77,8 @@ def test_paper_network_architecture(paper_net):
     assert (W, L, lam) == (64, 6, 1.5)
     assert len(linears) == 8 and sum(bn is not None for bn in norms) == 7 and norms[-1] is None
     assert [l[0].shape for l in linears] == [(64, 3)] + [(64, 64)] * 6 + [(1, 64)]
-    # weights and biases 25,281 plus 2 x 448 normalisation parameters: the
-    # paper's "about 30,000 network weights"
+    # weights and biases 25,281 plus 2 x 448 normalisation parameters, near
+    # the network size Sec. 5.2 gives
     assert params.size == 25281 == synth.mlp_param_count(64, 6)
     # the packed parameters are the fold of the trained layers
     P = np.random.default_rng(2).uniform(-1, 1, (300, 3))
