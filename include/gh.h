@@ -299,6 +299,14 @@ int gh_batch_graph_free(void *graph);
 int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim, int32_t tau_mode,
                               gh_mesh *out, void *stream);
 
+/* The order in which the hoppers take the N^2 columns (a column is i*N + j,
+ * i along x, j along y): the c-th claim of the queue gets column
+ * gh_column_order(N, c).  Square rings around the grid centre, innermost
+ * first, so the rays claimed last lie at the domain's edge.  A bijection of
+ * [0, N^2); returns -1 for N outside [1, 2048] or c outside [0, N^2).  Host
+ * only; no device work. */
+int64_t gh_column_order(int32_t N, int64_t c);
+
 /* Implicit-surface adjoint: given mesh vertices v[V][3] (device, float32) and
  * the loss gradient dL/dv[V][3] (device), writes
  *   dL/dtheta = sum_v s_v df/dtheta(v),  s_v = -(dL/dv . grad_x f)/|grad_x f|^2,

@@ -39,6 +39,11 @@ static int fail(int code, const char *fmt, ...) {
 extern "C" const char *gh_last_error(void) { return g_err.c_str(); }
 extern "C" const char *gh_version(void) { return "gridhop-gb300 0.1 (sm_103a)"; }
 
+extern "C" int64_t gh_column_order(int32_t N, int64_t c) {
+    if (N < 1 || N > 2048 || c < 0 || c >= (int64_t)N * N) return -1;
+    return (int64_t)column_of_claim((uint32_t)c, N);
+}
+
 // ---------------------------------------------------------------------------
 // Marching Cubes table.  Rule (the paper prints none): on each cube face,
 // walk the four corners counter-clockwise as seen from outside the cube;

@@ -88,6 +88,39 @@ __host__ __device__ inline float prim_bound_radius(const Prim &q) {
     return (float)(rb * (1.0 + 1e-6)) + 1e-6f;
 }
 
+// Order of the column queue: the c-th claimed column lies on the square ring
+// of side s around the grid centre (s = N mod 2, N mod 2 + 2, ...), innermost
+// rings first; within a ring, the top row, the bottom row, then the left and
+// right columns.  Rays near the middle of the domain, which usually cross
+// the surface and hop longest, start first, and the rays claimed last lie
+// at the domain's edge, which shortens the tail of the launch when the queue
+// runs dry.  A bijection of [0, N^2) for every N >= 1.
+__host__ __device__ inline uint32_t column_of_claim(uint32_t c, int N) {
+    uint32_t s = (uint32_t)sqrtf((float)c);
+    while (s * s > c) --s;
+    while ((s + 1) * (s + 1) <= c) ++s;
+    ++s;  // smallest side with s * s > c
+    if ((s & 1u) != ((uint32_t)N & 1u)) ++s;
+    const uint32_t lo = ((uint32_t)N - s) / 2, hi = lo + s - 1;
+    if (s == 1) return lo * (uint32_t)N + lo;
+    const uint32_t p = c - (s - 2) * (s - 2);
+    uint32_t i, j;
+    if (p < s) {
+        i = lo;
+        j = lo + p;
+    } else if (p < 2 * s) {
+        i = hi;
+        j = lo + p - s;
+    } else if (p < 3 * s - 2) {
+        i = lo + 1 + (p - 2 * s);
+        j = lo;
+    } else {
+        i = lo + 1 + (p - 3 * s + 2);
+        j = hi;
+    }
+    return i * (uint32_t)N + j;
+}
+
 // Length of the run of spheres starting at record i that the CSG fold
 // combines by min (record 0's op is never used, later records must be
 // unions); 0 when record i starts no such run.  The evaluator takes a run's

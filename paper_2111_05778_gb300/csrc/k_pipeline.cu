@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(512) k_hop_csg(const Item *__restrict__ items,
                 if (need) {
                     const unsigned long long c = base + __popc(needm & lt);
                     if (c < ncols) {
-                        col = (uint32_t)c;
+                        col = column_of_claim((uint32_t)c, N);
                         k = 0;
                         rank = 0;
                         const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);

@@ -108,6 +108,7 @@ def lib():
                                                              ctypes.POINTER(MeshDesc), P]),
                 "gh_last_profile": (ctypes.c_int, [ctypes.POINTER(Profile)]),
                 "gh_release_cache": (ctypes.c_int, []),
+                "gh_column_order": (I64, [I32, I64]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -122,7 +123,7 @@ def exported_symbols():
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
             "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc", "gh_batch_graph_launch",
-            "gh_batch_graph_free", "gh_release_cache"]
+            "gh_batch_graph_free", "gh_release_cache", "gh_column_order"]
 
 
 def check(rc):
@@ -518,3 +519,8 @@ def last_profile():
 
 def version() -> str:
     return lib().gh_version().decode()
+
+
+def column_order(N, c):
+    """gh_column_order: the column the c-th claim of the hoppers' queue takes."""
+    return int(lib().gh_column_order(int(N), int(c)))
