@@ -46,9 +46,11 @@ static constexpr unsigned FULL = 0xFFFFFFFFu;
 static constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
 
 // ---------------------------------------------------------------------------
-// Analytic SDB evaluation: exact distances of sphere, torus and box, folded
-// with min / max (Sec. 4.2-4.3).  Primitives are read from shared memory as
-// five float4 each (all lanes read the same primitive: broadcast).
+// Analytic SDB evaluation: exact distances of the seven primitives of
+// Sec. 5.1 (sphere, torus, box, capsule, capped cylinder, hexagonal prism,
+// cone), folded with min / max (Sec. 4.2-4.3).  Primitives are read from
+// shared memory as five float4 each (all lanes read the same primitive:
+// broadcast).
 // ---------------------------------------------------------------------------
 // Square root on the special-function unit (PTX sqrt.approx.f32, one
 // instruction instead of the correctly rounded sequence).  Its error is a
