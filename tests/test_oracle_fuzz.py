@@ -34,3 +34,15 @@ def test_random_scene_hop_equals_enumeration(seed, n, N, lo, span, tau_mode):
     assert _surface(mr) == set(er.cells.tolist())
     assert set(er.cells.tolist()) <= set(hr.marks.tolist())
     assert _tris(mr) == _tris(er)
+
+
+@hyp.settings(max_examples=20, deadline=None, derandomize=True)
+@hyp.given(seed=st.integers(0, 10_000), width=st.sampled_from([16, 32]), N=st.integers(6, 28),
+           tau_mode=st.sampled_from([oracle.TAU_DIAGONAL, oracle.TAU_HALF_DIAGONAL]))
+def test_random_network_hop_equals_enumeration(seed, width, N, tau_mode):
+    s = oracle.mlp(width, synth.MLP_NMID, synth.mlp_params(seed, width).astype(np.float64))
+    hr, mr = oracle.polygonize(s, N, tau_mode=tau_mode)
+    er = oracle.enum(s, N)
+    assert len(er.cells) > 0
+    assert _surface(mr) == set(er.cells.tolist())
+    assert _tris(mr) == _tris(er)
