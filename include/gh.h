@@ -289,11 +289,17 @@ int gh_batch_graph_free(void *graph);
  * more cells, or needs more lattice vertices, than the array holds returns
  * GH_ERR_CAPACITY with a message giving both numbers; N above the maximum
  * returns GH_ERR_ARG.  The first call on a device looks up the device
- * address of the array (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call uses the same
- * array and leaves its contents behind (each call clears its own counters
- * before use), so calls that overlap on the GPU -- from different streams or
- * threads at the same time -- race; serialise them. */
+ * address of the array (cudaGetSymbolAddress) with that device current and
+ * keeps it for later calls; make that first call before any stream capture.
+ * The kept address belongs to the device's primary context: after
+ * cudaDeviceReset on that device this entry point must not be called again
+ * in the process.  Before returning, every call waits for its stream and
+ * reads the device counters back to the host (that is how it reports
+ * GH_ERR_CAPACITY and GH_ERR_NONFINITE).  Every call uses the same array and
+ * leaves its contents behind (each call clears its own counters before use),
+ * so calls that overlap on the GPU -- from different streams or threads at
+ * the same time -- race; serialise them.  Devices with an ordinal of 64 or
+ * more get GH_ERR_DEVICE. */
 #define GH_NOALLOC_MAX_N 256
 #define GH_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim, int32_t tau_mode,

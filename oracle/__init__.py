@@ -83,12 +83,18 @@ def lib():
             L.or_csg_adjoint.restype = I
             L.or_csg_adjoint.argtypes = [P, I64, P, P, P]
             L.or_num_threads.restype = I
+            L.or_set_threads.argtypes = [I]
             _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Host threads of later oracle calls (n < 1: all cores)."""
+    lib().or_set_threads(int(n))
 
 
 def _ptr(a: np.ndarray):
@@ -113,6 +119,21 @@ class SDB:
         p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
         out = np.empty(p.shape[0], np.float64)
         lib().or_eval(self.h, p.shape[0], _ptr(p), _ptr(out))
+        return out
+
+    def eval_many(self, pts, chunk: int = 1 << 16) -> np.ndarray:
+        """f at many points: the C evaluator, except for a neural SDB, whose
+        layers then run as numpy matrix products (np_eval: the same
+        definition, a matrix product per layer as the only library step;
+        about 3x faster than the C loops for 10^6 points)."""
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        args = getattr(self, "np_args", None)
+        if args is None or p.shape[0] < 4096:
+            return self.eval(p)
+        params, width, nmid, kw = args
+        out = np.empty(p.shape[0], np.float64)
+        for s in range(0, p.shape[0], chunk):
+            out[s:s + chunk] = np_eval(params, width, nmid, p[s:s + chunk], **kw)
         return out
 
     def grad_x(self, pts) -> np.ndarray:
@@ -165,7 +186,9 @@ def mlp(width, nmid, params, r0=0.6, alpha=0.1, beta=1.1, lam=1.0, radial=True) 
     if a.size != n:
         raise ValueError("expected %d parameters, got %d" % (n, a.size))
     h = lib().or_mlp_new(width, nmid, _ptr(a), r0, alpha, beta, lam, 1.0 if radial else 0.0)
-    return SDB(h, "mlp", n)
+    sdb = SDB(h, "mlp", n)
+    sdb.np_args = (a.copy(), int(width), int(nmid), dict(r0=r0, alpha=alpha, beta=beta, lam=lam, radial=radial))
+    return sdb
 
 
 def lattice(N, values, lo=-1.0, hi=1.0) -> SDB:

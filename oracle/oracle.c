@@ -1028,3 +1028,13 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Sets the number of host threads later oracle calls use (n < 1: all cores).
+ * Harness control only (timing a one-core run); no arithmetic changes. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}

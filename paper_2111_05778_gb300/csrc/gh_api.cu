@@ -1175,6 +1175,9 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     if (wants_index(*out)) return fail(GH_ERR_UNIMPLEMENTED, "gh_polygonize_csg_noalloc: no indexed mesh output");
     int dev, nsm;
     if ((rc = ensure_device(&dev, &nsm))) return rc;
+    constexpr int NDEV = (int)(sizeof(g_noalloc_addr) / sizeof(g_noalloc_addr[0]));
+    if (dev < 0 || dev >= NDEV)
+        return fail(GH_ERR_DEVICE, "gh_polygonize_csg_noalloc: device %d beyond the %d this library tracks", dev, NDEV);
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);

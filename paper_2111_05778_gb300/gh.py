@@ -478,18 +478,6 @@ def backward(sdb: Sdb, verts, dl_dv, stream=None):
     return out if isinstance(sdb, MlpSdb) else out.reshape(-1, 20)
 
 
-def unique_vertices(mesh: "Mesh"):
-    """Indexed mesh from the triangle soup: vertices deduplicated by edge key
-    (equal keys carry bit-identical positions), faces [T,3] into them."""
-    import torch
-
-    keys = mesh.tri_keys.reshape(-1)
-    uk, inv = torch.unique(keys, return_inverse=True)
-    verts = torch.empty((uk.numel(), 3), dtype=mesh.tri_xyz.dtype, device=keys.device)
-    verts[inv] = mesh.tri_xyz.reshape(-1, 3)
-    return verts, inv.reshape(-1, 3), uk
-
-
 def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):
     """f at points [n,3] (a torch CUDA float32 tensor) -> [n] float32."""
     import torch

@@ -50,34 +50,17 @@ def test_bf16_refine_full(width, N):
     eps = sdb.calibrate(N)
     m = gh.polygonize(sdb, N, precision="bf16", eps=eps, keys=True, cells=True)
     ref = oracle.enum(o, N)
-    st = parity.compare(m, o, N, ref=ref)
+    st = parity.compare(m, o, N, ref=ref, gsdb=sdb)
     assert st["cells"] > 1000
+    assert st["tie_cells"] + st["sign_flip_cells"] <= 8
     assert m.stats["refined_vertices"] > 0
     # identical mesh to the FP32 path: the surface cells' corners are FP32 values
     m32 = gh.polygonize(sdb, N, precision="fp32", keys=True)
     assert (meshutil.canonical_tris(m.tri_keys.cpu().numpy()) ==
             meshutil.canonical_tris(m32.tri_keys.cpu().numpy())).all()
-
-
-def test_bf16_c2_sampled_n1024():
-    """The C2 workload with BF16 + FP32 refinement at N = 1024, checked on the
-    sign-change cells of 48 random columns against the oracle."""
-    sdb, o = _pair(1, 256)
-    N = 1024
-    eps = sdb.calibrate(N)
-    m = gh.polygonize(sdb, N, precision="bf16", eps=eps, keys=True, cells=True)
-    rng = np.random.default_rng(8)
-    i = rng.integers(300, 724, 48)
-    j = rng.integers(300, 724, 48)
-    cols = np.unique(i * N + j)
-    _, ref = oracle.polygonize(o, N, cols=cols)
-    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.95)
-    assert st["cells"] > 40
-    m32 = gh.polygonize(sdb, N, precision="fp32", keys=True, cells=True)
-    assert m.stats["surface_cells"] == m32.stats["surface_cells"]
-    assert m.n_tris == m32.n_tris
-    # hops shrink by eps but stay O(N^2 log N): within a few percent of FP32
-    assert m.stats["hop_evals"] < 1.1 * m32.stats["hop_evals"]
+    ua, pa = meshutil.vertex_table(m.tri_keys.cpu().numpy(), m.tri_xyz.cpu().numpy())
+    ub, pb = meshutil.vertex_table(m32.tri_keys.cpu().numpy(), m32.tri_xyz.cpu().numpy())
+    assert np.array_equal(ua, ub) and np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
 
 
 def test_bf16_needs_eps():

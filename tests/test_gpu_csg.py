@@ -27,37 +27,45 @@ def _golden(N):
 @pytest.mark.parametrize("N", [16, 64, 256])
 def test_sphere_matches_oracle(N):
     prims = synth.sphere_prims(0.5)
-    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
     o = oracle.csg(prims)
     _, ref = oracle.polygonize(o, N)
-    st = parity.compare(m, o, N, ref=ref)
+    st = parity.compare(m, o, N, ref=ref, gsdb=sdb)
     g = _golden(N)
     assert m.stats["surface_cells"] == g[4]
     assert m.n_tris == g[6]
     assert m.stats["marked_cells"] == g[2]
     assert m.stats["hop_evals"] == g[1]
+    # the six lattice corners with f = 0 exactly, (+-0.5, 0, 0) and permutations,
+    # lie on grid points for these N; each touches at most 4 surface cells
     assert st["tie_cells"] <= 24
+    assert st["sign_flip_cells"] == 0
 
 
 @pytest.mark.parametrize("N,lo,hi", [(37, -1.0, 1.0), (100, -0.7, 0.9), (2, -1.0, 1.0), (129, -0.61, 0.61)])
 def test_ragged_and_offset_grids(N, lo, hi):
     prims = np.concatenate([synth.sphere_prims(0.45, (0.05, -0.1, 0.02)),
                             synth.prim_row(synth.TORUS, synth.UNION, [0.1, 0.2, -0.1], [0.3, 0.08])[None]])
-    m = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, lo=lo, hi=hi, keys=True, cells=True)
     o = oracle.csg(prims)
     ref = oracle.enum(o, N, lo, hi)
-    parity.compare(m, o, N, lo, hi, ref=ref)
+    st = parity.compare(m, o, N, lo, hi, ref=ref, gsdb=sdb)
+    assert st["tie_cells"] + st["sign_flip_cells"] <= 8
 
 
 @pytest.mark.parametrize("tau_mode", [0, 1])
 def test_csg_scene_full(tau_mode):
     prims = synth.csg_prims(0)
     N = 160
-    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True, tau_mode=tau_mode)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, keys=True, cells=True, tau_mode=tau_mode)
     o = oracle.csg(prims)
     ref = oracle.enum(o, N)
-    st = parity.compare(m, o, N, ref=ref)
+    st = parity.compare(m, o, N, ref=ref, gsdb=sdb)
     assert st["cells"] > 10000
+    assert st["tie_cells"] + st["sign_flip_cells"] <= 16
 
 
 def test_csg_c1_sampled_columns_n512():
@@ -65,15 +73,18 @@ def test_csg_c1_sampled_columns_n512():
     cell of 400 random columns and of two full z-slabs, checked cell by cell."""
     prims = synth.csg_prims(0)
     N = 512
-    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
     o = oracle.csg(prims)
     rng = np.random.default_rng(11)
     cols = np.unique(rng.choice(N * N, 400, replace=False))
     _, ref = oracle.polygonize(o, N, cols=cols)
-    parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols))
+    parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), gsdb=sdb)
     for k0 in (173, 301):
         ref = oracle.enum(o, N, kmin=k0, kmax=k0 + 1)
-        parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: (c % N) == k0)
+        st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: (c % N) == k0, gsdb=sdb)
+        assert st["cells"] > 1000
+        assert st["tie_cells"] + st["sign_flip_cells"] <= 8
 
 
 def test_no_surface_inside_domain():
@@ -134,7 +145,7 @@ def test_eval_points_matches_oracle():
     P = synth.uniform_points(3, 100000)
     f = gh.eval_points(sdb, torch.from_numpy(P).cuda()).cpu().numpy()
     ref = oracle.csg(prims).eval(P.astype(np.float64))
-    assert np.abs(f - ref).max() < parity.DELTA32
+    assert np.abs(f - ref).max() < parity.EVAL32
 
 
 @pytest.mark.parametrize("N", [2, 63, 100])
@@ -155,7 +166,7 @@ def test_enumeration_equals_hopping_and_oracle(N):
     assert (meshutil.canonical_tris(e.tri_keys.cpu().numpy()) ==
             meshutil.canonical_tris(hp.tri_keys.cpu().numpy())).all()
     o = oracle.csg(prims)
-    parity.compare(e, o, N, ref=oracle.enum(o, N))
+    parity.compare(e, o, N, ref=oracle.enum(o, N), gsdb=sdb)
 
 
 @pytest.mark.parametrize("N,lo,hi", [(141, -1.0, 1.0), (200, -0.8, 0.8)])
@@ -163,14 +174,15 @@ def test_primitive_scene_matches_oracle(N, lo, hi):
     """The seven primitives of the paper's first scene (Sec. 5.1), rotated, in
     a union: every cell against the oracle's enumeration."""
     prims = synth.primitive_scene(0)
-    m = gh.polygonize(gh.CsgSdb(prims), N, lo=lo, hi=hi, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, lo=lo, hi=hi, keys=True, cells=True)
     o = oracle.csg(prims)
     ref = oracle.enum(o, N, lo, hi)
-    # every vertex meets the propagated bound 1e-4 h + h DELTA32 / |fA - fB|;
+    # every vertex meets the propagated bound 1e-4 h + h delta32 / |fA - fB|;
     # the rotated flat faces (box, prism, cylinder caps, cone base) put more
     # lattice edges nearly tangent to the surface than curved shapes do, so
     # the share within the bare 1e-4 h is checked at 0.995
-    st = parity.compare(m, o, N, lo, hi, ref=ref, min_bare=0.995)
+    st = parity.compare(m, o, N, lo, hi, ref=ref, min_bare=0.995, gsdb=sdb)
     assert st["cells"] > 5000
 
 
@@ -185,7 +197,7 @@ def test_primitive_distances_match_oracle():
         P = rng.uniform(-0.6, 0.6, (20000, 3)).astype(np.float32)
         got = gh.eval_points(gh.CsgSdb(prims), torch.tensor(P, device="cuda")).cpu().numpy().astype(np.float64)
         ref = oracle.csg(prims).eval(P.astype(np.float64))
-        assert np.abs(got - ref).max() < parity.DELTA32, kind
+        assert np.abs(got - ref).max() < parity.EVAL32, kind
 
 
 def test_mixed_scene_eval_matches_oracle():
@@ -198,7 +210,7 @@ def test_mixed_scene_eval_matches_oracle():
     P = rng.uniform(-1.0, 1.0, (200000, 3)).astype(np.float32)
     got = gh.eval_points(gh.CsgSdb(prims), torch.tensor(P, device="cuda")).cpu().numpy().astype(np.float64)
     ref = oracle.csg(prims).eval(P.astype(np.float64))
-    assert np.abs(got - ref).max() < parity.DELTA32
+    assert np.abs(got - ref).max() < parity.EVAL32
 
 
 def test_scaled_rotation_rejected():
@@ -217,7 +229,8 @@ def test_mixed_scene_polygonize_matches_oracle():
     oracle's enumeration."""
     prims = synth.mixed_prims(7)
     N = 150
-    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
     o = oracle.csg(prims)
-    st = parity.compare(m, o, N, ref=oracle.enum(o, N), min_bare=0.995)
+    st = parity.compare(m, o, N, ref=oracle.enum(o, N), min_bare=0.995, gsdb=sdb)
     assert st["cells"] > 5000

@@ -17,17 +17,18 @@ N = 2048
 
 def test_csg_n2048_sampled_columns_and_slab():
     prims = synth.csg_prims(0)
-    m = gh.polygonize(gh.CsgSdb(prims), N, keys=True, cells=True)
+    sdb = gh.CsgSdb(prims)
+    m = gh.polygonize(sdb, N, keys=True, cells=True)
     o = oracle.csg(prims)
     rng = np.random.default_rng(31)
     cols = np.unique(rng.choice(N * N, 300, replace=False))
     _, ref = oracle.polygonize(o, N, cols=cols)
     # the bare 1e-4 h (1e-7) is below the FP32 evaluation error on nearly
     # tangent edges here; every vertex meets the propagated bound
-    parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.9)
+    parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.9, gsdb=sdb)
     k0 = 1234
     ref = oracle.enum(o, N, kmin=k0, kmax=k0 + 1)
-    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: (c % N) == k0, min_bare=0.9)
+    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: (c % N) == k0, min_bare=0.9, gsdb=sdb)
     assert st["cells"] > 1000
     assert m.stats["surface_cells"] > 4 * 400000  # about 4x the N = 1024 count
 
@@ -43,7 +44,8 @@ def test_neural_bf16_n2048_sampled_columns():
     j = rng.integers(600, 1448, 24)
     cols = np.unique(i * N + j)
     _, ref = oracle.polygonize(o, N, cols=cols)
-    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.9)
+    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.9,
+                        gsdb=sdb)
     assert st["cells"] > 40
     assert m.stats["surface_cells"] > 4 * 1_000_000
 

@@ -30,29 +30,9 @@ def test_mlp_fp32_full(width, N):
     sdb, o = _pair(1 + width, width)
     m = gh.polygonize(sdb, N, keys=True, cells=True)
     ref = oracle.enum(o, N)
-    st = parity.compare(m, o, N, ref=ref)
+    st = parity.compare(m, o, N, ref=ref, gsdb=sdb)
     assert st["cells"] > 1000
-
-
-def test_mlp_c2_fp32_sampled_n1024():
-    """The C2 network (seed 1, width 256) at N = 1024 in FP32: the sign-change
-    cells of 48 random columns, checked cell by cell against the oracle."""
-    sdb, o = _pair(1, 256)
-    N = 1024
-    m = gh.polygonize(sdb, N, keys=True, cells=True)
-    rng = np.random.default_rng(7)
-    # columns through the middle of the domain so that they cross the surface
-    i = rng.integers(300, 724, 48)
-    j = rng.integers(300, 724, 48)
-    cols = np.unique(i * N + j)
-    _, ref = oracle.polygonize(o, N, cols=cols)
-    # at h = 2/1024 the bare 1e-4 h (2e-7) is about the FP32 evaluation error
-    # of this network divided by |fA - fB| on nearly tangent edges, so ~2% of
-    # the vertices exceed it; all stay inside the error-propagated bound.
-    st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), min_bare=0.95)
-    assert st["cells"] > 40
-    s = m.stats
-    assert s["surface_cells"] > 1_000_000
+    assert st["tie_cells"] + st["sign_flip_cells"] <= 8
 
 
 def test_enumeration_equals_hopping_mlp():
@@ -64,6 +44,6 @@ def test_enumeration_equals_hopping_mlp():
     ke, pe = meshutil.vertex_table(e.tri_keys.cpu().numpy(), e.tri_xyz.cpu().numpy())
     kh, ph = meshutil.vertex_table(hp.tri_keys.cpu().numpy(), hp.tri_xyz.cpu().numpy())
     assert (ke == kh).all() and np.array_equal(pe, ph)
-    parity.compare(e, o, N, ref=oracle.enum(o, N))
+    parity.compare(e, o, N, ref=oracle.enum(o, N), gsdb=sdb)
     with pytest.raises(gh.GhError):
         gh.polygonize(sdb, N, method="enum", precision="bf16", eps=1e-5)

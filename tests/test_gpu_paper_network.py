@@ -29,7 +29,7 @@ def test_paper_network_eval_matches_oracle(net):
     P = torch.from_numpy(synth.uniform_points(21, 50001)).cuda()
     f = gh.eval_points(sdb, P, "fp32").cpu().numpy().astype(np.float64)
     ref = o.eval(P.cpu().numpy().astype(np.float64))
-    assert np.abs(f - ref).max() < parity.DELTA32
+    assert np.abs(f - ref).max() < parity.EVAL32
 
 
 @pytest.mark.parametrize("N,lo,hi", [(100, -1.0, 1.0), (77, -0.9, 0.85)])
@@ -37,7 +37,7 @@ def test_paper_network_fp32_matches_oracle(net, N, lo, hi):
     params, W, L, lam, sdb, o = net
     m = gh.polygonize(sdb, N, lo=lo, hi=hi, keys=True, cells=True)
     ref = oracle.enum(o, N, lo, hi)
-    st = parity.compare(m, o, N, lo, hi, ref=ref)
+    st = parity.compare(m, o, N, lo, hi, ref=ref, gsdb=sdb)
     assert st["cells"] > 3000
 
 
@@ -46,7 +46,7 @@ def test_paper_network_bf16_refine(net):
     N = 128
     eps = sdb.calibrate(N)
     m = gh.polygonize(sdb, N, precision="bf16", eps=eps, keys=True, cells=True)
-    parity.compare(m, o, N, ref=oracle.enum(o, N))
+    parity.compare(m, o, N, ref=oracle.enum(o, N), gsdb=sdb)
     m32 = gh.polygonize(sdb, N, precision="fp32", keys=True)
     assert (meshutil.canonical_tris(m.tri_keys.cpu().numpy()) ==
             meshutil.canonical_tris(m32.tri_keys.cpu().numpy())).all()

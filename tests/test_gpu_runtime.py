@@ -38,7 +38,7 @@ def test_pooled_scratch_gives_identical_meshes():
     c = gh.CsgSdb(prims)
     mc = gh.polygonize(c, 96, keys=True, cells=True)
     o = oracle.csg(prims)
-    parity.compare(mc, o, 96, ref=oracle.enum(o, 96))
+    parity.compare(mc, o, 96, ref=oracle.enum(o, 96), gsdb=c)
     c.close()
     gh.release_cache()
     d = gh.MlpSdb(p, 128)
@@ -53,5 +53,5 @@ def test_device_weight_layouts_match_oracle_in_both_engines():
     ref = o.eval(P.cpu().numpy().astype(np.float64))
     f32 = gh.eval_points(sdb, P, "fp32").cpu().numpy().astype(np.float64)
     f16 = gh.eval_points(sdb, P, "bf16").cpu().numpy().astype(np.float64)
-    assert np.abs(f32 - ref).max() < parity.DELTA32
+    assert np.abs(f32 - ref).max() < parity.EVAL32
     assert np.abs(f16 - ref).max() < 2e-4
