@@ -1,14 +1,20 @@
 """Benchmark of the grid-hopping polygonizer on one GB300 (or N replicas).
 
-Workload: the neural SDB f(p) = (|p| - 0.6 + 0.1 g(p)) / 1.1, g a seeded
-spectrally normalised ReLU MLP 3 -> 256 x 6 -> 1, polygonized on an N = 1024
-grid over [-1, 1]^3 (synthetic stand-in for the paper's learned SDBs,
+Headline workload: the neural SDB f(p) = (|p| - 0.6 + 0.1 g(p)) / 1.1, g a
+seeded spectrally normalised ReLU MLP 3 -> 256 x 6 -> 1, polygonized on an
+N = 1024 grid over [-1, 1]^3 (synthetic stand-in for the paper's learned SDBs,
 Sec. 5.2).  One step = one whole polygonization (ray hopping, vertex lists,
 vertex evaluation, FP32 refinement, Marching Cubes) through gh_polygonize.
 
 Metric: surface cells per second (sign-change cells / ms per mesh), the
 headline path being BF16 tensor-core hopping with FP32 refinement; the plain
-FP32 path is timed beside it.  Prints one JSON line (rank 0).
+FP32 path is timed beside it.  After the headline's timed region the other
+workloads are timed the same way and reported under "workloads": the sphere
+at N = 64, the analytic CSG scene at N = 512, the batch of 64 SDBs replayed
+as one CUDA graph, and the implicit adjoint at N = 256.  Last, on the host
+cores, the CPU baseline leg times the FP64 oracle on bounded samples of every
+workload and compares the GPU results with the oracle's on those samples
+("accuracy").  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -19,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -33,7 +40,23 @@ WORKLOAD = {
     "workload": "neural SDB seed 1 (MLP 3->256x6->1, spectral-normalised, ReLU), N=1024, [-1,1]^3",
     "sdb": "mlp", "seed": 1, "width": 256, "N": 1024,
 }
-FLOP_PER_EVAL = 2 * (3 * 256 + 5 * 256 * 256 + 256)  # weights only: 657,408
+
+
+def mlp_flop(width, n_mid=5):
+    """Algorithmic FLOP of one neural-SDB evaluation (weights only)."""
+    return 2 * (3 * width + n_mid * width * width + width)
+
+
+FLOP_PER_EVAL = mlp_flop(256)  # 657,408
+
+# FLOP of one primitive's exact distance as written (an FMA counts 2, a
+# square root 1), rotation into the local frame included; plus one min/max of
+# the fold.  One analytic evaluation = the whole fold over all primitives.
+PRIM_FLOP = {0: 11, 1: 29, 2: 38, 3: 30, 4: 32, 5: 45, 6: 50}
+
+
+def csg_flop(prims):
+    return int(sum(PRIM_FLOP[int(t)] for t in np.asarray(prims)[:, 0]))
 
 
 def parse():
@@ -44,11 +67,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-workloads", action="store_true", help="time the headline workload only")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--N", type=int, default=None, help="grid size (default 1024; smaller for profiling)")
     ap.add_argument("--workload", default="neural", choices=["neural", "batch", "csg", "adjoint", "crossover"],
-                    help="neural: one N=1024 neural SDB (default); batch: the 64-item batch, graph-replayed; "
-                         "csg: the analytic scene at N=512; adjoint: gh_backward on the N=256 neural mesh")
+                    help="neural: one N=1024 neural SDB (default, with the other workloads after it); "
+                         "batch / csg / adjoint: that workload alone; crossover: hopping vs enumeration")
     args = ap.parse_args()
     if args.N:
         WORKLOAD["N"] = int(args.N)
@@ -84,16 +108,25 @@ def aggregate_replicas(total_ms, units, steps, world, device="cpu"):
 
 
 # ---------------------------------------------------------------------------
-# oracle on the host cores (CPU baseline / reference arm)
+# The oracle on the host cores: the CPU baseline leg and the reference arm.
+# Everything below that runs oracle code is called only from cpu_leg() (after
+# every GPU timed region) and from run_reference().
 # ---------------------------------------------------------------------------
-def oracle_sample(seconds: float, seed: int = 123):
-    """Times the FP64 oracle (serial hopper + Marching Cubes) on random columns
-    of the workload grid; returns (surface cells per second, cores, sample)."""
+def _oracle_mlp(seed, width):
     import oracle
     from paper_2111_05778_gb300 import synth
 
+    return oracle.mlp(width, synth.MLP_NMID, synth.mlp_params(seed, width).astype(np.float64))
+
+
+def oracle_sample(seconds: float, seed: int = 123, osdb=None):
+    """Times the FP64 oracle (serial hopper + Marching Cubes) on random columns
+    of the headline grid; returns (surface cells per second, cores, sample,
+    seconds, columns, MC result)."""
+    import oracle
+
     N, W = WORKLOAD["N"], WORKLOAD["width"]
-    o = oracle.mlp(W, synth.MLP_NMID, synth.mlp_params(WORKLOAD["seed"], W).astype(np.float64))
+    o = osdb if osdb is not None else _oracle_mlp(WORKLOAD["seed"], W)
     rng = np.random.default_rng(seed)
     cols_all = rng.permutation(N * N)
     n = 256
@@ -106,8 +139,9 @@ def oracle_sample(seconds: float, seed: int = 123):
         _, mr = oracle.polygonize(o, N, cols=cols_all[:n])
         dt = time.perf_counter() - t0
     surf = int(((mr.cases > 0) & (mr.cases < 255)).sum())
-    return surf / dt, oracle.num_threads(), "%d uniformly random columns of the N=%d grid (%.1f s, %d surface cells)" % (
-        n, N, dt, surf), dt
+    return (surf / dt, oracle.num_threads(),
+            "%d uniformly random columns of the N=%d grid (%.1f s, %d surface cells)" % (n, N, dt, surf), dt,
+            np.sort(cols_all[:n]), mr)
 
 
 def run_reference(args):
@@ -120,7 +154,7 @@ def run_reference(args):
         oracle_sample(1.0, seed=900 + k)
     vals, secs = [], []
     for k in range(args.steps):
-        v, cores, sample, dt = oracle_sample(per_step, seed=123 + k)
+        v, cores, sample, dt, _, _ = oracle_sample(per_step, seed=123 + k)
         vals.append(v)
         secs.append(dt)
     value = float(np.median(vals))
@@ -135,9 +169,131 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------------------
-# GPU arm
-# ---------------------------------------------------------------------------
+def _parity():
+    tests = os.path.join(ROOT, "tests")
+    if tests not in sys.path:
+        sys.path.insert(0, tests)
+    import parity
+
+    return parity
+
+
+def _acc(st, N, stats=None):
+    """The accuracy record of one comparison (parity.compare, reporting form)."""
+    out = {"cells_compared": st["cells"], "tie_cells_1e-6h": st["tie_cells"],
+           "fp32_sign_flip_cells": st["sign_flip_cells"], "mismatched_cells": st["mismatched_cells"],
+           "mismatched_triangles": st["mismatched_tris"], "vertices_compared": st["verts"],
+           "vertices_over_tolerance": st["vertices_over_tol"], "max_vertex_err_over_h": st["max_err_over_h"],
+           "share_within_1e-4h": st["bare_frac"], "delta32": st["delta32"]}
+    if stats is not None and N > 1:
+        out["hops_per_N2log2N"] = stats["hop_evals"] / (N * N * math.log2(N))
+    return out
+
+
+def _timed_oracle(fn, threads=0):
+    import oracle
+
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    r = fn()
+    dt = time.perf_counter() - t0
+    oracle.set_threads(0)
+    return dt, r
+
+
+def cpu_leg(ctx, seconds):
+    """The oracle on bounded samples of every workload (all host cores, and
+    one core for the small ones), and the GPU results compared with the
+    oracle's on the same samples.  Returns (cpu_baseline record of the
+    headline, accuracy of the headline, {workload: {"oracle": ..,
+    "accuracy": ..}})."""
+    import oracle
+
+    par = _parity()
+    out = {}
+    # ---- headline: random columns of the N = 1024 grid ------------------------
+    c2 = ctx["c2"]
+    N = WORKLOAD["N"]
+    o2 = _oracle_mlp(WORKLOAD["seed"], WORKLOAD["width"])
+    v, cores, sample, dt, cols, mr = oracle_sample(seconds, osdb=o2)
+    hr_cols = oracle.hop(o2, N, cols=cols[:512])
+    evals_per_s = float(hr_cols.col_evals.sum()) / _timed_oracle(lambda: oracle.hop(o2, N, cols=cols[:512]))[0]
+    cpu = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample,
+           "full_mesh_s_extrapolated": c2["stats"]["surface_cells"] / v,
+           "enum_s_extrapolated": 8.0 * N ** 3 / evals_per_s,
+           "note": "ghop = the oracle's serial hopper + Marching Cubes; enum = Marching Cubes on all N^3 cells "
+                   "(8 evaluations each), extrapolated from the measured evaluation rate"}
+    inside = lambda c: np.isin(c // N, cols)
+    acc = {}
+    for prec, m in c2["meshes"].items():
+        st = par.compare(m, o2, N, ref=mr, restrict_cells=inside, gsdb=c2["gsdb"], check=False)
+        acc[prec] = _acc(st, N, m.stats)
+    acc["sample"] = "the CPU baseline's %d columns" % cols.size
+    # ---- sphere N = 64: the whole grid, all cores and one core ---------------
+    if "c0" in ctx:
+        c = ctx["c0"]
+        o = oracle.csg(c["prims"])
+        t_all, (hr, mrr) = _timed_oracle(lambda: oracle.polygonize(o, c["N"]))
+        t_one, _ = _timed_oracle(lambda: oracle.polygonize(o, c["N"]), threads=1)
+        e_all, er = _timed_oracle(lambda: oracle.enum(o, c["N"]))
+        e_one, _ = _timed_oracle(lambda: oracle.enum(o, c["N"]), threads=1)
+        st = par.compare(c["mesh"], o, c["N"], ref=mrr, gsdb=c["gsdb"], check=False)
+        out["C0"] = {"oracle": {"ghop_s": t_all, "ghop_s_1core": t_one, "enum_s": e_all, "enum_s_1core": e_one,
+                                "cores": cores, "hop_evals": int(hr.col_evals.sum())},
+                     "accuracy": dict(_acc(st, c["N"], c["mesh"].stats), sample="every cell")}
+    # ---- CSG N = 512: sampled columns and one slab, all cores and one core ----
+    if "c1" in ctx:
+        c = ctx["c1"]
+        n1 = c["N"]
+        o = oracle.csg(c["prims"])
+        rng = np.random.default_rng(5)
+        cs = np.sort(rng.choice(n1 * n1, 4000, replace=False))
+        t_all, (_, mrr) = _timed_oracle(lambda: oracle.polygonize(o, n1, cols=cs))
+        t_one, _ = _timed_oracle(lambda: oracle.polygonize(o, n1, cols=cs[:1000]), threads=1)
+        k0 = n1 // 2 + 7
+        e_all, er = _timed_oracle(lambda: oracle.enum(o, n1, kmin=k0, kmax=k0 + 1))
+        st = par.compare(c["mesh"], o, n1, ref=mrr, restrict_cells=lambda x: np.isin(x // n1, cs), gsdb=c["gsdb"],
+                         check=False)
+        st2 = par.compare(c["mesh"], o, n1, ref=er, restrict_cells=lambda x: (x % n1) == k0, gsdb=c["gsdb"],
+                          check=False)
+        out["C1"] = {"oracle": {"ghop_s_extrapolated": t_all * n1 * n1 / cs.size,
+                                "ghop_s_1core_extrapolated": t_one * n1 * n1 / 1000,
+                                "enum_s_extrapolated": e_all * n1, "cores": cores,
+                                "sample": "4000 random columns (1000 on one core); enum: one z-slab"},
+                     "accuracy": {"columns": _acc(st, n1, c["mesh"].stats), "slab_k%d" % k0: _acc(st2, n1)}}
+    # ---- batch: 16 random columns of every item -------------------------------
+    if "c3" in ctx:
+        t_sum, worst, rows = 0.0, {}, 0
+        for kind, seed, n, w, gsdb, m, prims in ctx["c3"]["items"]:
+            o = oracle.csg(prims) if kind == "csg" else _oracle_mlp(seed, w)
+            rng = np.random.default_rng(1000 + seed)
+            cs = np.sort(rng.choice(n * n, 16, replace=False))
+            dt_i, (_, mrr) = _timed_oracle(lambda: oracle.polygonize(o, n, cols=cs))
+            t_sum += dt_i * n * n / cs.size
+            st = par.compare(m, o, n, ref=mrr, restrict_cells=lambda x: np.isin(x // n, cs), gsdb=gsdb,
+                             check=False)
+            rows += st["cells"]
+            for key in ("mismatched_cells", "mismatched_triangles", "vertices_over_tolerance",
+                        "max_vertex_err_over_h"):
+                a = _acc(st, n)[key]
+                worst[key] = max(worst.get(key, 0), a)
+        worst["cells_compared"] = rows
+        out["C3"] = {"oracle": {"ghop_s_extrapolated": t_sum, "cores": cores,
+                                "sample": "16 random columns of each of the 64 items"},
+                     "accuracy": dict(worst, sample="16 random columns of each item (worst item shown)")}
+    # ---- adjoint: the FP64 adjoint on the same vertices ---------------------------
+    if "c4" in ctx:
+        c = ctx["c4"]
+        V = c["verts"].cpu().numpy().astype(np.float64)
+        G = c["dldv"].cpu().numpy().astype(np.float64)
+        t_all, g64 = _timed_oracle(lambda: oracle.np_adjoint(c["params"].astype(np.float64), c["W"], 5, V, G))
+        g = c["grad"].cpu().numpy().astype(np.float64)
+        scale = np.abs(g64).max()
+        rel = np.abs(g - g64) / np.maximum(np.abs(g64), 1e-2 * scale)
+        out["C4"] = {"oracle": {"adjoint_s": t_all, "cores": cores, "kind": "numpy FP64 adjoint (oracle.np_adjoint)"},
+                     "accuracy": {"max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel)),
+                                  "metric": "|g - g64| / max(|g64|, 1e-2 max|g64|) over all parameters"}}
+    return cpu, acc, out
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -191,6 +347,35 @@ def measured_peaks():
         "fallback"
 
 
+
+
+def _events(stream):
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed(fn, steps, warmup, flush, stream):
+    """Mean CUDA-event ms of fn over `steps` runs after `warmup` runs, the L2
+    flushed (a 256 MB buffer written) between runs."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+        flush.zero_()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        a, b = _events(stream)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        flush.zero_()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.mean(ts))
+
+
 def run_ours(args):
     import torch
 
@@ -232,8 +417,8 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    hop_ms, phases_sum = [], {}
+    ev = [_events(stream) for _ in range(args.steps)]
+    phases_sum = {}
     launches = 0
     for i in range(args.steps):
         ev[i][0].record(stream)
@@ -241,7 +426,6 @@ def run_ours(args):
         ev[i][1].record(stream)
         n_l, ph = gh.last_profile()  # waits for this step's phase events
         launches += n_l
-        hop_ms.append(ph.get("hop", float("nan")))
         for k, v in ph.items():
             phases_sum[k] = phases_sum.get(k, 0.0) + v
         flush.zero_()
@@ -266,6 +450,16 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = e2e_measure(gh, torch, params, W, N, precision, eps, cap, max(2, min(args.steps, 5)), stream)
+    if precision == "bf16":
+        e2e["eps"] = "calibrated once per SDB before the timed region (gh_sdb_calibrate), not in this number"
+        cal = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sdb.calibrate(N)
+            cal.append((time.perf_counter() - t0) * 1e3)
+        e2e["calibrate_ms"] = float(np.median(cal))
+        e2e["value_with_calibration"] = cells / ((e2e["ms_per_mesh"] + e2e["calibrate_ms"]) / 1e3)
 
     line = {
         "metric": "surface cells/s", "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
@@ -274,23 +468,38 @@ def run_ours(args):
         "config": dict(WORKLOAD, precision="bf16+fp32-refine" if precision == "bf16" else "fp32",
                        l2="256 MB buffer written between timed steps (L2 flush)", replicas=world),
         "ms_per_mesh": ms, "surface_cells": cells, "triangles": st["triangles"], "hop_evals": st["hop_evals"],
+        "hops_per_N2log2N": st["hop_evals"] / (N * N * math.log2(N)),
         "marked_cells": st["marked_cells"], "unique_vertices": st["unique_vertices"],
         "refined_vertices": st["refined_vertices"],
         "hop_row_utilization": st["hop_evals"] / st["row_slots"] if st.get("row_slots") else None,
         "phases_ms": phase_ms,
         "roofline": roof, "kernels": kern, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
+    ctx = {}
     if precision == "bf16":
         line["fp32_path"] = fp32_companion(gh, torch, sdb, N, bufs, stream, flush)
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        v, cores, sample, _ = oracle_sample(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+    solo = rank == 0 and world == 1
+    if solo and not args.no_cpu_baseline:
+        meshes = {precision: gh.polygonize(sdb, N, precision=precision, eps=eps, keys=True, cells=True)}
+        if precision == "bf16":
+            meshes["fp32"] = gh.polygonize(sdb, N, precision="fp32", keys=True, cells=True)
+        ctx["c2"] = {"gsdb": sdb, "meshes": meshes, "stats": st}
+    if solo and not args.no_workloads:
+        line["workloads"] = {}
+        for name, fn in (("C0", work_c0), ("C1", work_c1), ("C3", work_c3), ("C4", work_c4)):
+            rec, c = fn(args, flush, stream)
+            line["workloads"][name] = rec
+            ctx[name.lower()] = c
+    if solo and not args.no_cpu_baseline:
+        cpu, acc, per = cpu_leg(ctx, args.cpu_seconds)
+        line["cpu_baseline"] = cpu
+        line["accuracy"] = acc
+        for name, rec in per.items():
+            line["workloads"].setdefault(name, {}).update(rec)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
 def _src_hash(rel):
     import hashlib
 
@@ -344,6 +553,9 @@ def kernel_rooflines(precision, st, phase_ms, peaks, peak_kind):
     else:
         row("k_hop_mlp_fp32<256>", "hop", st["hop_evals"], "alu")
         row("k_pts_mlp_fp32<256,0>", "vertices", st["unique_vertices"], "alu")
+    mc = mesh_write_row(st, WORKLOAD["N"], phase_ms.get("mc"), peaks, peak_kind)
+    if mc:
+        rows.append(mc)
     return rows
 
 
@@ -404,100 +616,41 @@ def e2e_measure(gh, torch, params, W, N, precision, eps, cap, steps, stream):
             "d2h_bytes_per_step": d2h}
 
 
-BATCH_WORKLOAD = {
-    "workload": "batch of 64 SDBs (seeds 0..63: even CSG 24 spheres + 8 tori - 4 boxes, odd neural MLP width "
-                "64/128/256), N in {128..1024}, one CUDA graph",
-}
 
 
-def run_batch(args):
-    """The 64-item batch: hopping in one persistent launch per evaluator
-    family, the whole sequence captured in a CUDA graph and replayed."""
-    import torch
-
-    from paper_2111_05778_gb300 import gh, synth, tune
-
-    torch.cuda.set_device(0)
-    items = synth.batch_items(64)
-    sdbs, Ns = [], []
-    for kind, seed, N, W in items:
-        if kind == "csg":
-            s = gh.CsgSdb(synth.csg_prims(seed))
-        else:
-            s = gh.MlpSdb(synth.mlp_params(seed, W), W)
-            s.calibrate(N, n_points=1 << 18)
-        sdbs.append(s)
-        Ns.append(N)
-    precision = "bf16" if args.precision in ("auto", "bf16") else "fp32"
-    rb, mt, timings = tune.tune_batch(sdbs, Ns, precision=precision, use_cache=False)
-    base = gh.polygonize_batch(sdbs, Ns, precision=precision, ray_block=rb, mlp_tiles=mt)
-    caps = [int(c * 1.05) + 4096 for c in base.counts()]
-    bt = gh.Batch(sdbs, Ns, caps, precision=precision, ray_block=rb, mlp_tiles=mt)
-    bt.capture()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        bt.replay()
-        flush.zero_()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    ts = []
-    for _ in range(args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        bt.replay()
-        b.record(stream)
-        flush.zero_()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    clk = clocks.stop()
-    stats = [bt.bufs[i].stats_dict() for i in range(len(sdbs))]
-    cells = sum(st["surface_cells"] for st in stats)
-    ms = float(np.mean(ts))
-    line = {
-        "metric": "surface cells/s", "value": cells / (ms / 1e3), "unit": "cells/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if precision == "bf16" else "f32", "data": "synthetic",
-        "config": dict(BATCH_WORKLOAD, precision=precision, ray_block=rb, mlp_tiles=mt,
-                       l2="256 MB buffer written between timed steps (L2 flush)"),
-        "meshes": len(sdbs), "ms_per_mesh": ms / len(sdbs), "surface_cells": cells,
-        "triangles": sum(st["triangles"] for st in stats), "autotune_ms": timings, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
+# ---------------------------------------------------------------------------
+# The other workloads, each timed on its own after the headline's timed region
+# ---------------------------------------------------------------------------
+def _alu_row(kernel, flop, ms, peaks):
+    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = flop / (ms / 1e3) / 1e12
+    return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": ach / fp32_peak, "traffic": None, "kernel_ms": ms, "flop_per_launch": flop,
+            "peak_source": "FP32: 152 SMs x 128 lanes x 2 FLOP x max SM clock (derived)"}
 
 
-def _timed(fn, steps, warmup, flush, stream):
-    import torch
-
-    for _ in range(warmup):
-        fn()
-        flush.zero_()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        flush.zero_()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    return float(np.mean(ts))
+def mesh_write_row(st, N, ms, peaks, peak_kind):
+    """k_mc (Marching Cubes on the marked cells) against HBM: algorithmic
+    bytes = the soup written (36 B per triangle) + the marks read (8 B per
+    marked cell) + the vertex list read once (8 B key + 4 B value per lattice
+    vertex) + the line offsets (4 B per lattice line)."""
+    if not ms:
+        return None
+    T, M, V = st["triangles"], st["marked_cells"], st["unique_vertices"]
+    byts = 36 * T + 8 * M + 12 * V + 4 * (N + 1) ** 2
+    ach = byts / (ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    return {"kernel": "k_mc", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": ncu_traffic("k_mc", M), "kernel_ms": ms, "bytes_per_launch": byts,
+            "mesh_bytes": 36 * T, "peak_source": "hbm_gbs (%s)" % peak_kind}
 
 
-def run_csg(args):
-    """The analytic scene (CSG seed 0: 24 spheres + 8 tori - 4 boxes) at N = 512, FP32."""
-    import torch
+def _csg_workload(prims, N, args, flush, stream, name):
+    from paper_2111_05778_gb300 import gh
 
-    from paper_2111_05778_gb300 import gh, synth
-
-    torch.cuda.set_device(0)
-    N = args.N or 512
-    sdb = gh.CsgSdb(synth.csg_prims(0))
+    sdb = gh.CsgSdb(prims)
     probe = gh.polygonize(sdb, N)
     bufs = gh.Buffers(int(probe.n_tris * 1.05) + 4096)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
     gh.set_profiling(True)
     phases = {}
 
@@ -508,52 +661,133 @@ def run_csg(args):
             phases.setdefault(k, []).append(v)
 
     clocks = ClockSampler(0)
-    ms = _timed(step, args.steps, args.warmup, flush, stream)
+    steps = max(args.steps, 10)
+    ms = _timed(step, steps, args.warmup, flush, stream)
     clk = clocks.stop()
     st = bufs.stats_dict()
-    line = {"metric": "surface cells/s", "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "analytic CSG seed 0 (24 spheres + 8 tori - 4 boxes), N=%d, [-1,1]^3" % N},
-            "ms_per_mesh": ms, "phases_ms": {k: float(np.mean(v[args.warmup:] or v)) for k, v in phases.items()},
-            "hop_evals": st["hop_evals"], "marked_cells": st["marked_cells"],
-            "unique_vertices": st["unique_vertices"], "surface_cells": st["surface_cells"],
-            "triangles": st["triangles"], "clocks": clk}
-    print(json.dumps(line), flush=True)
+    assert st["status"] == 0, st
+    ph = {k: float(np.mean(v[-steps:])) for k, v in phases.items()}
+    peaks, peak_kind = measured_peaks()
+    kern = [_alu_row("k_hop_csg", st["hop_evals"] * csg_flop(prims), ph["hop"], peaks),
+            _alu_row("k_eval_vertices_csg", st["unique_vertices"] * csg_flop(prims), ph["vertices"], peaks),
+            mesh_write_row(st, N, ph["mc"], peaks, peak_kind)]
+    rec = {"workload": name, "ms_per_mesh": ms, "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
+           "dtype": "f32", "steps": steps, "phases_ms": ph, "hop_evals": st["hop_evals"],
+           "hops_per_N2log2N": st["hop_evals"] / (N * N * math.log2(N)), "marked_cells": st["marked_cells"],
+           "unique_vertices": st["unique_vertices"], "surface_cells": st["surface_cells"],
+           "triangles": st["triangles"], "flop_per_eval": csg_flop(prims),
+           "roofline": dict(max(kern, key=lambda r: r["kernel_ms"])), "kernels": kern, "clocks": clk}
+    mesh = gh.polygonize(sdb, N, keys=True, cells=True)
+    return rec, {"prims": prims, "gsdb": sdb, "mesh": mesh, "N": N}
 
 
-def run_adjoint(args):
+def work_c0(args, flush, stream):
+    from paper_2111_05778_gb300 import synth
+
+    return _csg_workload(synth.sphere_prims(0.5), 64, args, flush, stream,
+                         "analytic sphere |p| - 0.5, N=64, [-1,1]^3, FP32")
+
+
+def work_c1(args, flush, stream):
+    from paper_2111_05778_gb300 import synth
+
+    return _csg_workload(synth.csg_prims(0), args.N if args.workload == "csg" and args.N else 512, args, flush,
+                         stream, "analytic CSG seed 0 (24 spheres + 8 tori - 4 boxes), N=512, [-1,1]^3, FP32")
+
+
+BATCH_WORKLOAD = ("batch of 64 SDBs (seeds 0..63: even CSG 24 spheres + 8 tori - 4 boxes, odd neural MLP width "
+                  "64/128/256), N in {128..1024}, one CUDA graph")
+
+
+def work_c3(args, flush, stream):
+    """The 64-item batch: hopping in one persistent launch per evaluator
+    family, the whole sequence captured in a CUDA graph and replayed."""
+    from paper_2111_05778_gb300 import gh, synth, tune
+
+    items = synth.batch_items(64)
+    sdbs, Ns, prims_of = [], [], []
+    t0 = time.perf_counter()
+    for kind, seed, N, W in items:
+        if kind == "csg":
+            p = synth.csg_prims(seed)
+            s = gh.CsgSdb(p)
+        else:
+            p = None
+            s = gh.MlpSdb(synth.mlp_params(seed, W), W)
+            s.calibrate(N, n_points=1 << 18)
+        sdbs.append(s)
+        Ns.append(N)
+        prims_of.append(p)
+    setup_s = time.perf_counter() - t0
+    precision = "bf16" if args.precision in ("auto", "bf16") else "fp32"
+    rb, mt, timings = tune.tune_batch(sdbs, Ns, precision=precision, use_cache=False)
+    base = gh.polygonize_batch(sdbs, Ns, precision=precision, ray_block=rb, mlp_tiles=mt)
+    caps = [int(c * 1.05) + 4096 for c in base.counts()]
+    bt = gh.Batch(sdbs, Ns, caps, precision=precision, ray_block=rb, mlp_tiles=mt)
+    bt.capture()
+    clocks = ClockSampler(0)
+    steps = max(args.steps, 5)
+    ms = _timed(bt.replay, steps, args.warmup, flush, stream)
+    clk = clocks.stop()
+    stats = [bt.bufs[i].stats_dict() for i in range(len(sdbs))]
+    assert all(st["status"] == 0 for st in stats)
+    cells = sum(st["surface_cells"] for st in stats)
+    peaks, peak_kind = measured_peaks()
+    tensor_flop = sum((st["hop_evals"] + st["unique_vertices"]) * mlp_flop(W)
+                      for (kind, _, _, W), st in zip(items, stats) if kind == "mlp") if precision == "bf16" else 0
+    fp32_flop = sum(st["refined_vertices"] * mlp_flop(W) for (kind, _, _, W), st in zip(items, stats)
+                    if kind == "mlp")
+    bf16_peak = float(peaks.get("bf16_tflops", 1917.8))
+    ach = tensor_flop / (ms / 1e3) / 1e12
+    rec = {"workload": BATCH_WORKLOAD, "ms_per_batch": ms, "ms_per_mesh": ms / len(sdbs),
+           "value": cells / (ms / 1e3), "unit": "cells/s", "dtype": "bf16" if precision == "bf16" else "f32",
+           "steps": steps, "meshes": len(sdbs), "surface_cells": cells,
+           "triangles": sum(st["triangles"] for st in stats), "ray_block": rb, "mlp_tiles": mt,
+           "autotune_ms": timings, "setup_s": setup_s,
+           "roofline": {"kernel": "whole batch (graph replay)", "bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                        "unit": "TFLOP/s", "frac": ach / bf16_peak, "traffic": None,
+                        "note": "BF16 tensor FLOP of the neural items (hop + vertex evaluations) over the whole "
+                                "batch time (analytic items, FP32 refinement (%.2f TFLOP), lists and Marching "
+                                "Cubes included in the time)" % (fp32_flop / 1e12),
+                        "peak_source": "bf16_tflops (%s)" % peak_kind},
+           "clocks": clk}
+    chk = gh.polygonize_batch(sdbs, Ns, precision=precision, keys=True, cells=True, ray_block=rb, mlp_tiles=mt)
+    ctx = {"items": [(kind, seed, N, W, sdbs[b], chk.mesh(b), prims_of[b])
+                     for b, (kind, seed, N, W) in enumerate(items)]}
+    bt.close()
+    return rec, ctx
+
+
+def work_c4(args, flush, stream):
     """gh_backward for the C4 workload: the width-256 network of seed 1, its
     N = 256 FP32 mesh, loss = mean over unique vertices of (|v - c| - 0.55)^2."""
     import torch
 
     from paper_2111_05778_gb300 import gh, synth
 
-    torch.cuda.set_device(0)
-    W, N = 256, args.N or 256
-    sdb = gh.MlpSdb(synth.mlp_params(1, W), W)
+    W, N = 256, 256
+    params = synth.mlp_params(1, W)
+    sdb = gh.MlpSdb(params, W)
     verts = gh.polygonize(sdb, N, indexed=True).verts  # one vertex per crossing edge, on the device
     c = torch.tensor(np.random.default_rng(4).uniform(-0.05, 0.05, 3), dtype=torch.float32, device="cuda")
     v = verts.clone().requires_grad_(True)
     loss = ((v - c).norm(dim=1) - 0.55).pow(2).mean()
     loss.backward()
     dldv = v.grad.detach()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    ms = _timed(lambda: gh.backward(sdb, verts, dldv), args.steps, args.warmup, flush, stream)
+    clocks = ClockSampler(0)
+    steps = max(args.steps, 10)
+    ms = _timed(lambda: gh.backward(sdb, verts, dldv), steps, args.warmup, flush, stream)
+    clk = clocks.stop()
     V = verts.shape[0]
-    flop = V * 2 * (3 * W + 5 * W * W + W) * 3  # forward, delta chain, weight sums (weights only)
-    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
-    line = {"metric": "adjoint vertices/s", "value": V / (ms / 1e3), "unit": "vertices/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "implicit adjoint, neural SDB seed 1 width 256, N=%d mesh, %d vertices" % (N, V)},
-            "roofline": {"bound": "alu", "achieved": flop / (ms / 1e3) / 1e12, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": flop / (ms / 1e3) / 1e12 / fp32_peak, "traffic": None,
-                         "kernel": "gh_backward (all kernels)"}}
-    print(json.dumps(line), flush=True)
-
-
+    flop = V * mlp_flop(W) * 3  # forward, delta chain, weight sums (weights only)
+    peaks, _ = measured_peaks()
+    row = _alu_row("gh_backward (all kernels)", flop, ms, peaks)
+    rec = {"workload": "implicit adjoint, neural SDB seed 1 width 256, N=%d mesh, %d vertices" % (N, V),
+           "metric": "adjoint vertices/s", "ms": ms, "value": V / (ms / 1e3), "unit": "vertices/s", "dtype": "f32",
+           "steps": steps, "vertices": V, "roofline": row, "clocks": clk}
+    grad = gh.backward(sdb, verts, dldv)
+    torch.cuda.synchronize()
+    return rec, {"verts": verts, "dldv": dldv, "grad": grad, "params": params, "W": W}
 def run_crossover(args):
     """Grid hopping against enumeration (Sec. 2: every lattice point and cell)
     on the same GPU, for the analytic scene, the width-256 network and a
@@ -593,6 +827,27 @@ def run_crossover(args):
     print(json.dumps({"workload": "crossover", "rows": rows}), flush=True)
 
 
+def run_single(args):
+    """One of the other workloads alone, as its own bench line."""
+    import torch
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    fn = {"csg": work_c1, "batch": work_c3, "adjoint": work_c4}[args.workload]
+    rec, _ = fn(args, flush, stream)
+    ms = rec.get("ms_per_mesh", rec.get("ms_per_batch", rec.get("ms")))
+    if args.workload == "batch":
+        ms = rec["ms_per_batch"]
+    line = {"metric": rec.get("metric", "surface cells/s"), "value": rec["value"], "unit": rec["unit"],
+            "n_gpus": 1, "steps": rec["steps"], "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"],
+            "data": "synthetic", "config": {"workload": rec["workload"],
+                                            "l2": "256 MB buffer written between timed steps (L2 flush)"},
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "detail": rec}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "crossover":
@@ -600,12 +855,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch":
-        run_batch(args)
-    elif args.workload == "csg":
-        run_csg(args)
-    elif args.workload == "adjoint":
-        run_adjoint(args)
+    elif args.workload in ("batch", "csg", "adjoint"):
+        run_single(args)
     else:
         run_ours(args)
 

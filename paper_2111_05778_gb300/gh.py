@@ -365,11 +365,12 @@ class Batch:
     graph of the same launches that replay() re-runs."""
 
     def __init__(self, sdbs, Ns, caps, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0,
-                 mlp_tiles=0, indexed=False):
+                 mlp_tiles=0, indexed=False, cells=False):
         self.sdbs = list(sdbs)
         self.Ns = [int(n) for n in Ns]
         self.B = len(self.sdbs)
-        self.bufs = [Buffers(c, keys=keys, cap_verts=(c // 2 + 4096) if indexed else 0) for c in caps]
+        self.bufs = [Buffers(c, keys=keys, cap_cells=c if cells else 0, cap_verts=(c // 2 + 4096) if indexed else 0)
+                     for c in caps]
         self.grids = (Grid * self.B)(*[_grid(n, lo, hi) for n in self.Ns])
         self.handles = (ctypes.c_void_p * self.B)(*[s_.handle for s_ in self.sdbs])
         self.meshes = (MeshDesc * self.B)(*[b.desc for b in self.bufs])
@@ -408,24 +409,27 @@ class Batch:
     def counts(self):
         import torch
 
-        # triangles needed, or twice the mesh vertices when those overflowed
-        return torch.stack([torch.maximum(b.counts[0], 2 * b.counts[2]) for b in self.bufs]).cpu().numpy()
+        # triangles (or surface cells) needed, or twice the mesh vertices when those overflowed
+        return torch.stack([torch.maximum(torch.maximum(b.counts[0], b.counts[1]), 2 * b.counts[2])
+                            for b in self.bufs]).cpu().numpy()
 
     def mesh(self, b) -> "Mesh":
         bb = self.bufs[b]
-        T, _, V = [int(x) for x in bb.counts.cpu().numpy()]
+        T, C, V = [int(x) for x in bb.counts.cpu().numpy()]
         ind = bb.verts is not None
-        return Mesh(bb.tri_xyz[:T], bb.tri_keys[:T] if bb.tri_keys is not None else None, None, None,
+        cl = bb.cell_ids is not None
+        return Mesh(bb.tri_xyz[:T], bb.tri_keys[:T] if bb.tri_keys is not None else None,
+                    bb.cell_ids[:C] if cl else None, bb.cell_cases[:C] if cl else None,
                     bb.stats_dict(), bb.verts[:V] if ind else None, bb.faces[:T] if ind else None)
 
 
 def polygonize_batch(sdbs, Ns, lo=-1.0, hi=1.0, precision="fp32", keys=False, eps=None, ray_block=0, mlp_tiles=0,
-                     indexed=False):
+                     indexed=False, cells=False):
     """gh_polygonize_batch with per-item buffers sized automatically; returns
     the Batch (its meshes via .mesh(b))."""
     caps = [4 * n * n + 4096 for n in Ns]
     for _ in range(3):
-        bt = Batch(sdbs, Ns, caps, lo, hi, precision, keys, eps, ray_block, mlp_tiles, indexed)
+        bt = Batch(sdbs, Ns, caps, lo, hi, precision, keys, eps, ray_block, mlp_tiles, indexed, cells)
         rc = bt.run(sync=True)
         if rc == GH_OK:
             return bt

@@ -201,21 +201,24 @@ def compare(gpu, osdb, N, lo=-1.0, hi=1.0, ref=None, restrict_cells=None, gsdb=N
           "vertices_over_tol": int((err > tol).sum()),
           "max_err_over_h": float(err.max() / h) if err.size else 0.0, "bare_frac": bare}
     if check:
-        assert excl.size <= limit, "%d cells excluded (%d in the 1e-6 h band, %d FP32 sign flips) > %d" % (
-            excl.size, st["tie_cells"], st["sign_flip_cells"], limit)
-        assert gset.size == oset.size and (gset == oset).all(), (
-            "surface cells differ: %d only on GPU, %d only in oracle" % (np.setdiff1d(gset, oset).size,
-                                                                         np.setdiff1d(oset, gset).size))
-        assert not bad_case, "case index differs in %d cells, e.g. %d: gpu %d oracle %d" % (
-            len(bad_case), bad_case[0], gmap[bad_case[0]], omap[bad_case[0]])
-        assert ct_g.shape == ct_o.shape, "triangle counts differ: gpu %d oracle %d" % (ct_g.shape[0],
-                                                                                       ct_o.shape[0])
-        assert tri_mismatch == 0, "triangle edge-key multisets differ"
-        assert uk_g.size == uk_o.size == kk.size
-        worst = np.argmax(err - tol) if err.size else 0
-        assert (err <= tol).all(), "vertex error %.3g > tol %.3g (h = %.3g, delta32 = %.3g)" % (
-            err[worst], tol[worst], h, delta32)
-        assert bare >= min_bare, "only %.5f of vertices within 1e-4 h" % bare
+        try:
+            assert excl.size <= limit, "%d cells excluded (%d in the 1e-6 h band, %d FP32 sign flips) > %d" % (
+                excl.size, st["tie_cells"], st["sign_flip_cells"], limit)
+            assert gset.size == oset.size and (gset == oset).all(), (
+                "surface cells differ: %d only on GPU, %d only in oracle" % (np.setdiff1d(gset, oset).size,
+                                                                             np.setdiff1d(oset, gset).size))
+            assert not bad_case, "case index differs in %d cells, e.g. %d: gpu %d oracle %d" % (
+                len(bad_case), bad_case[0], gmap[bad_case[0]], omap[bad_case[0]])
+            assert ct_g.shape == ct_o.shape, "triangle counts differ: gpu %d oracle %d" % (ct_g.shape[0],
+                                                                                           ct_o.shape[0])
+            assert tri_mismatch == 0, "triangle edge-key multisets differ"
+            assert uk_g.size == uk_o.size == kk.size
+            worst = np.argmax(err - tol) if err.size else 0
+            assert (err <= tol).all(), "vertex error %.3g > tol %.3g (h = %.3g, delta32 = %.3g)" % (
+                err[worst], tol[worst], h, delta32)
+            assert bare >= min_bare, "only %.5f of vertices within 1e-4 h" % bare
+        except AssertionError as e:
+            raise AssertionError("%s | stats: %r" % (e, st)) from None
     return st
 
 
