@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "bf16x6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="time the headline workload only")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -226,7 +226,7 @@ def cpu_leg(ctx, seconds):
     inside = lambda c: np.isin(c // N, cols)
     acc = {}
     for prec, m in c2["meshes"].items():
-        st = par.compare(m, o2, N, ref=mr, restrict_cells=inside, gsdb=c2["gsdb"], check=False)
+        st = par.compare(m, o2, N, ref=mr, restrict_cells=inside, gsdb=c2["gsdb"], check=False, gprec=prec)
         acc[prec] = _acc(st, N, m.stats)
     acc["sample"] = "the CPU baseline's %d columns" % cols.size
     # ---- sphere N = 64: the whole grid, all cores and one core ---------------
@@ -395,7 +395,7 @@ def run_ours(args):
     if precision == "auto":
         precision = "bf16" if _bf16_available(sdb) else "fp32"
     eps = None
-    if precision == "bf16":
+    if precision in ("bf16", "bf16x6"):
         eps = sdb.calibrate(N)
 
     # size the buffers with one synchronous call
@@ -450,7 +450,7 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = e2e_measure(gh, torch, params, W, N, precision, eps, cap, max(2, min(args.steps, 5)), stream)
-    if precision == "bf16":
+    if precision != "fp32":
         e2e["eps"] = "calibrated once per SDB before the timed region (gh_sdb_calibrate), not in this number"
         cal = []
         for _ in range(3):
@@ -464,8 +464,9 @@ def run_ours(args):
     line = {
         "metric": "surface cells/s", "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if precision == "bf16" else "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, precision="bf16+fp32-refine" if precision == "bf16" else "fp32",
+        "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "bf16", "data": "synthetic",
+        "config": dict(WORKLOAD, precision={"bf16": "bf16+fp32-refine", "bf16x6": "bf16+split-bf16x6-refine",
+                                            "fp32": "fp32"}[precision],
                        l2="256 MB buffer written between timed steps (L2 flush)", replicas=world),
         "ms_per_mesh": ms, "surface_cells": cells, "triangles": st["triangles"], "hop_evals": st["hop_evals"],
         "hops_per_N2log2N": st["hop_evals"] / (N * N * math.log2(N)),
@@ -476,13 +477,16 @@ def run_ours(args):
         "roofline": roof, "kernels": kern, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
     ctx = {}
-    if precision == "bf16":
-        line["fp32_path"] = fp32_companion(gh, torch, sdb, N, bufs, stream, flush)
+    if precision != "fp32":
+        line["fp32_path"] = companion(gh, torch, sdb, N, bufs, stream, flush, "fp32")
+        line["bf16x6_refine_path"] = companion(gh, torch, sdb, N, bufs, stream, flush, "bf16x6", eps)
     solo = rank == 0 and world == 1
     if solo and not args.no_cpu_baseline:
         meshes = {precision: gh.polygonize(sdb, N, precision=precision, eps=eps, keys=True, cells=True)}
-        if precision == "bf16":
-            meshes["fp32"] = gh.polygonize(sdb, N, precision="fp32", keys=True, cells=True)
+        for extra in ("fp32", "bf16", "bf16x6"):
+            if precision != "fp32" and extra not in meshes:
+                meshes[extra] = gh.polygonize(sdb, N, precision=extra, eps=None if extra == "fp32" else eps,
+                                              keys=True, cells=True)
         ctx["c2"] = {"gsdb": sdb, "meshes": meshes, "stats": st}
     if solo and not args.no_workloads:
         line["workloads"] = {}
@@ -546,10 +550,21 @@ def kernel_rooflines(precision, st, phase_ms, peaks, peak_kind):
                      "peak_source": ("bf16_tflops (%s)" % peak_kind) if bound == "tensor" else
                      "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x %.0f MHz (derived)" % sm_max})
 
-    if precision == "bf16":
+    if precision in ("bf16", "bf16x6"):
         row("k_mlp_bf16<256,0,2>", "hop", st["hop_evals"], "tensor")
         row("k_mlp_bf16<256,1,2>", "vertices", st["unique_vertices"], "tensor")
-        row("k_pts_mlp_fp32<256,1>", "refine", st["refined_vertices"], "alu")
+        if precision == "bf16":
+            row("k_pts_mlp_fp32<256,1>", "refine", st["refined_vertices"], "alu")
+        elif phase_ms.get("refine"):
+            # six BF16 tensor products per hidden-layer product (executed FLOP)
+            fl = st["refined_vertices"] * 6 * 2 * 5 * 256 * 256
+            ms = phase_ms["refine"]
+            ach = fl / (ms / 1e3) / 1e12
+            rows.append({"kernel": "k_mlp_x6<256,0>", "bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                         "unit": "TFLOP/s", "frac": ach / bf16_peak, "traffic": ncu_traffic("k_mlp_x6<256,0>",
+                         st["refined_vertices"]), "kernel_ms": ms, "flop_per_launch": fl,
+                         "units_per_launch": st["refined_vertices"],
+                         "peak_source": "bf16_tflops (%s)" % peak_kind})
     else:
         row("k_hop_mlp_fp32<256>", "hop", st["hop_evals"], "alu")
         row("k_pts_mlp_fp32<256,0>", "vertices", st["unique_vertices"], "alu")
@@ -569,23 +584,38 @@ def _bf16_available(sdb):
         return False
 
 
-def fp32_companion(gh, torch, sdb, N, bufs, stream, flush, steps=3):
-    gh.polygonize_into(sdb, N, bufs, precision="fp32", sync=True, stream=stream)
-    ts = []
+def companion(gh, torch, sdb, N, bufs, stream, flush, precision="fp32", eps=None, steps=3):
+    """The same workload in another precision, a few steps (not the headline)."""
+    gh.polygonize_into(sdb, N, bufs, precision=precision, eps=eps, sync=True, stream=stream)
+    ts, phs = [], []
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        gh.polygonize_into(sdb, N, bufs, precision="fp32", sync=False, stream=stream)
+        gh.polygonize_into(sdb, N, bufs, precision=precision, eps=eps, sync=False, stream=stream)
         b.record(stream)
         _, ph = gh.last_profile()
         flush.zero_()
         torch.cuda.synchronize()
-        ts.append((a.elapsed_time(b), ph.get("hop", float("nan"))))
+        ts.append(a.elapsed_time(b))
+        phs.append(ph)
     st = bufs.stats_dict()
-    ms = float(np.mean([t[0] for t in ts]))
-    hop = float(np.mean([t[1] for t in ts]))
-    return {"ms_per_mesh": ms, "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
-            "hop_ms": hop, "hop_tflops": st["hop_evals"] * FLOP_PER_EVAL / (hop / 1e3) / 1e12}
+    assert st["status"] == 0, st
+    ms = float(np.mean(ts))
+    ph = {k: float(np.mean([p[k] for p in phs])) for k in phs[0]}
+    out = {"precision": precision, "ms_per_mesh": ms, "value": st["surface_cells"] / (ms / 1e3), "unit": "cells/s",
+           "phases_ms": ph, "hop_tflops": st["hop_evals"] * FLOP_PER_EVAL / (ph["hop"] / 1e3) / 1e12}
+    if precision == "bf16x6":
+        peaks, peak_kind = measured_peaks()
+        W = WORKLOAD["width"]
+        tensor = st["refined_vertices"] * 6 * 2 * 5 * W * W  # six BF16 products per hidden-layer product
+        ach = tensor / (ph["refine"] / 1e3) / 1e12
+        bf = float(peaks.get("bf16_tflops", 1917.8))
+        out["refine_roofline"] = {
+            "kernel": "k_mlp_x6<256,0>", "bound": "tensor", "achieved": ach, "peak": bf, "unit": "TFLOP/s",
+            "frac": ach / bf, "traffic": None, "kernel_ms": ph["refine"], "units_per_launch": st["refined_vertices"],
+            "flop_per_launch": tensor, "peak_source": "bf16_tflops (%s)" % peak_kind,
+            "fp32_equivalent_tflops": st["refined_vertices"] * FLOP_PER_EVAL / (ph["refine"] / 1e3) / 1e12}
+    return out
 
 
 def e2e_measure(gh, torch, params, W, N, precision, eps, cap, steps, stream):
@@ -719,7 +749,7 @@ def work_c3(args, flush, stream):
         Ns.append(N)
         prims_of.append(p)
     setup_s = time.perf_counter() - t0
-    precision = "bf16" if args.precision in ("auto", "bf16") else "fp32"
+    precision = "bf16" if args.precision == "auto" else args.precision
     rb, mt, timings = tune.tune_batch(sdbs, Ns, precision=precision, use_cache=False)
     base = gh.polygonize_batch(sdbs, Ns, precision=precision, ray_block=rb, mlp_tiles=mt)
     caps = [int(c * 1.05) + 4096 for c in base.counts()]
@@ -734,13 +764,13 @@ def work_c3(args, flush, stream):
     cells = sum(st["surface_cells"] for st in stats)
     peaks, peak_kind = measured_peaks()
     tensor_flop = sum((st["hop_evals"] + st["unique_vertices"]) * mlp_flop(W)
-                      for (kind, _, _, W), st in zip(items, stats) if kind == "mlp") if precision == "bf16" else 0
+                      for (kind, _, _, W), st in zip(items, stats) if kind == "mlp") if precision != "fp32" else 0
     fp32_flop = sum(st["refined_vertices"] * mlp_flop(W) for (kind, _, _, W), st in zip(items, stats)
                     if kind == "mlp")
     bf16_peak = float(peaks.get("bf16_tflops", 1917.8))
     ach = tensor_flop / (ms / 1e3) / 1e12
     rec = {"workload": BATCH_WORKLOAD, "ms_per_batch": ms, "ms_per_mesh": ms / len(sdbs),
-           "value": cells / (ms / 1e3), "unit": "cells/s", "dtype": "bf16" if precision == "bf16" else "f32",
+           "value": cells / (ms / 1e3), "unit": "cells/s", "dtype": "f32" if precision == "fp32" else "bf16",
            "steps": steps, "meshes": len(sdbs), "surface_cells": cells,
            "triangles": sum(st["triangles"] for st in stats), "ray_block": rb, "mlp_tiles": mt,
            "autotune_ms": timings, "setup_s": setup_s,

@@ -127,11 +127,20 @@ typedef struct {
 #define GH_FP32 0        /* every evaluation in FP32                           */
 #define GH_BF16_REFINE 1 /* neural SDB: hop in BF16 with an error bound eps,   */
                          /* corners of candidate cells re-evaluated in FP32    */
+/* GH_BF16_REFINE_X6: as GH_BF16_REFINE, but the corners are re-evaluated on
+ * the tensor cores with split-BF16 products instead of FP32 FMAs: every FP32
+ * operand of a hidden layer is split exactly into three BF16 parts and the
+ * six part products of size >= 2^-16 of the product are accumulated in FP32
+ * (the dropped three are below about 2^-23 of it).  Not FP32 arithmetic:
+ * its error against exact arithmetic is of FP32's size, not bit-identical to
+ * GH_FP32.  gh_eval takes it too (points evaluated that way). */
+#define GH_BF16_REFINE_X6 2
 #define GH_TAU_DIAGONAL 0      /* tau = sqrt(3) h: one cell diagonal (default) */
 #define GH_TAU_HALF_DIAGONAL 1 /* tau = sqrt(3) h / 2: the tightest safe value */
 
 typedef struct {
-    int32_t precision; /* GH_FP32 | GH_BF16_REFINE (MLP only)                 */
+    int32_t precision; /* GH_FP32 | GH_BF16_REFINE | GH_BF16_REFINE_X6       */
+                       /* (the two BF16 modes: neural SDBs only)             */
     int32_t tau_mode;  /* GH_TAU_*                                            */
     float eps;         /* BF16 bound |f_bf16 - f_fp32| <= eps/2; < 0 = the    */
                        /* SDB's calibrated value (gh_sdb_calibrate)           */

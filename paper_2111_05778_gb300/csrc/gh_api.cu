@@ -334,13 +334,13 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     // in place from the uploaded block
     const size_t WW = (size_t)W * W;
     float *d_wt, *d_wtb, *d_bm;
-    uint16_t *d_wbf;
+    uint16_t *d_wbf, *d_wx6;
     if (dev_alloc(s, &s->d_params, (size_t)np) || dev_alloc(s, &d_wt, (size_t)h.n_mid * WW) ||
         dev_alloc(s, &d_wtb, (size_t)h.n_mid * WW) || dev_alloc(s, &d_bm, (size_t)h.n_mid * W) ||
-        dev_alloc(s, &d_wbf, (size_t)h.n_mid * WW))
+        dev_alloc(s, &d_wbf, (size_t)h.n_mid * WW) || dev_alloc(s, &d_wx6, (size_t)3 * h.n_mid * WW))
         return GH_ERR_CUDA;
     GH_CUDA(cudaMemcpy(s->d_params, P, sizeof(float) * np, cudaMemcpyHostToDevice));
-    launch_prep_mlp(s->d_params, W, h.n_mid, d_wt, d_wtb, d_wbf, d_bm, 0);
+    launch_prep_mlp(s->d_params, W, h.n_mid, d_wt, d_wtb, d_wbf, d_wx6, d_bm, 0);
     GH_CUDA(cudaGetLastError());
     GH_CUDA(cudaStreamSynchronize(0));  // the layouts are complete before any stream uses them
     const float *d_w0 = s->d_params, *d_b0 = s->d_params + 3 * W;
@@ -361,6 +361,7 @@ static int create_mlp(gh_sdb *s, const gh_sdb_desc *d) {
     m.wout = d_wout;
     m.bout = wout[W];
     m.wbf = d_wbf;
+    m.wx6 = d_wx6;
     s->nparam = np;
     return GH_OK;
 }
@@ -667,7 +668,8 @@ static int enqueue_once(gh_sdb *s, const GridP &g, const gh_options &o, const gh
         mark_phase(3, st);
         launch_refine_select(g, c, st);
         mark_phase(4, st);
-        launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, true, st);
+        if (o.precision == GH_BF16_REFINE_X6) launch_refine_mlp_x6(s->d_item, 1, s->mlp.width, nsm, st);
+        else launch_eval_vertices_mlp_fp32(s->d_item, 1, s->mlp.width, nsm, true, st);
         mark_phase(5, st);
         launches += LAUNCHES_REFINE;
     }
@@ -696,10 +698,10 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         return fail(GH_ERR_UNIMPLEMENTED, "the enumeration method runs in FP32 only");
     if (o.method == GH_METHOD_ENUM && wants_index(*out))
         return fail(GH_ERR_UNIMPLEMENTED, "the indexed mesh output needs GH_METHOD_HOP");
-    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
+    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE && o.precision != GH_BF16_REFINE_X6)
         return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
-    if (o.precision == GH_BF16_REFINE) {
-        if (s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "GH_BF16_REFINE applies to neural SDBs only");
+    if (o.precision != GH_FP32) {
+        if (s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "the BF16 precisions apply to neural SDBs only");
         if (!bf16_supported(s->mlp.width))
             return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path not available for width %d", s->mlp.width);
         if (s->mlp.n_mid > bf16_max_mid())
@@ -763,6 +765,10 @@ extern "C" int gh_eval(const gh_sdb *s, const float *p, int64_t n, float *out, i
         if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid())
             return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width / depth");
         launch_eval_points_mlp_bf16(s->mlp, p, n, out, nsm, st);
+    } else if (precision == GH_BF16_REFINE_X6) {
+        if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > x6_max_mid())
+            return fail(GH_ERR_UNIMPLEMENTED, "no split-BF16 path for this width / depth");
+        launch_eval_points_mlp_x6(s->mlp, p, n, out, nsm, st);
     } else {
         return fail(GH_ERR_ARG, "unknown precision %d", precision);
     }
@@ -896,7 +902,8 @@ static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_
                 const int b = P.order[q];
                 launch_refine_select(P.g[b], sd[b]->scr, st);
             }
-            launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, true, st);
+            if (o.precision == GH_BF16_REFINE_X6) launch_refine_mlp_x6(di, n, first->mlp.width, nsm, st);
+            else launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, true, st);
         }
     }
     for (int b = 0; b < B; ++b) {
@@ -913,7 +920,7 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
     if (B < 1 || !grids || !sdbs || !outs) return fail(GH_ERR_ARG, "gh_polygonize_batch: empty or NULL arguments");
     gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0, GH_METHOD_HOP};
     if (opts) o = *opts;
-    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE)
+    if (o.precision != GH_FP32 && o.precision != GH_BF16_REFINE && o.precision != GH_BF16_REFINE_X6)
         return fail(GH_ERR_ARG, "unknown precision %d", o.precision);
     if (o.method != GH_METHOD_HOP) return fail(GH_ERR_UNIMPLEMENTED, "batches run grid hopping only");
     int dev, nsm, rc;
@@ -929,7 +936,7 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
         if (sd[b]->device != dev) return fail(GH_ERR_ARG, "item %d: SDB on another device", b);
         if ((rc = check_grid(&grids[b], &P.g[b], o.tau_mode))) return rc;
         if ((rc = check_mesh(&outs[b]))) return rc;
-        if (sd[b]->kind == GH_SDB_MLP && o.precision == GH_BF16_REFINE) {
+        if (sd[b]->kind == GH_SDB_MLP && o.precision != GH_FP32) {
             if (sd[b]->mlp.n_mid > bf16_max_mid())
                 return fail(GH_ERR_UNIMPLEMENTED, "item %d: BF16 path supports at most %d hidden layers", b,
                             bf16_max_mid());

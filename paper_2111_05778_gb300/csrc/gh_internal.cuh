@@ -144,6 +144,7 @@ struct MlpDev {
     const float *wout;  // [W]
     float bout;
     const uint16_t *wbf;  // n_mid x BF16 hidden weights in the tensor-core tile layout
+    const uint16_t *wx6;  // n_mid x 3 BF16 parts (low, middle, high) of the hidden weights, same layout
 };
 
 // Scratch of one polygonization (device pointers) and its capacities.
@@ -232,14 +233,18 @@ void launch_eval_vertices_mlp_bf16(const Item *items, int n_items, int width, in
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,
                                  cudaStream_t st);
 void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st);  // k_pipeline.cu
+// neural SDB with split-BF16 tensor-core products (k_mlp_x6.cu)
+int x6_max_mid();
+void launch_refine_mlp_x6(const Item *items, int n_items, int width, int nsm, cudaStream_t st);
+void launch_eval_points_mlp_x6(const MlpDev &m, const float *p, long long n, float *out, int nsm, cudaStream_t st);
 // exclusive scan of n uint32 into out[0..n] (k_pipeline.cu); bsum holds
 // ceil(n / 4096) partials; *total gets the sum
 void scan_u32_dev(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
                   Counters *ctr, cudaStream_t st);
 long long scan_partials(long long n);
 // derived weight layouts of a neural SDB from its packed parameters (k_prep.cu)
-void launch_prep_mlp(const float *params, int W, int n_mid, float *wt, float *wtb, uint16_t *wbf, float *bm,
-                     cudaStream_t st);
+void launch_prep_mlp(const float *params, int W, int n_mid, float *wt, float *wtb, uint16_t *wbf, uint16_t *wx6,
+                     float *bm, cudaStream_t st);
 // indexed mesh output after Marching Cubes (k_index.cu)
 void launch_index_mesh(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
 

@@ -11,6 +11,10 @@
 //       (row n, 16-byte chunk c of inputs [8c, 8c+8) at
 //       (n/8)*1024 + (n%8)*128 + ((c ^ n%8) * 16)), BF16 rounded to nearest
 //       even;
+//   wx6 (split-BF16 engine): per layer three BF16 parts of every weight,
+//       w = w_h + w_m + w_l exactly (w_h = bf16(w), w_m = bf16(w - w_h),
+//       w_l = bf16(w - w_h - w_m)), stored part by part (low, middle, high),
+//       each part in wbf's layout;
 //   bm  hidden biases, n_mid x [W].
 #include "gh_internal.cuh"
 
@@ -23,9 +27,17 @@ __device__ __forceinline__ int perm_pos(int o) {
     return (m >> 2) * 64 + og * 4 + (m & 3);
 }
 
+// BF16 of an FP32 value, rounded to nearest even (finite values)
+__device__ __forceinline__ uint16_t bf16_rne(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
 __global__ void __launch_bounds__(256) k_prep_mlp(const float *__restrict__ params, int W, int n_mid,
                                                   float *__restrict__ wt, float *__restrict__ wtb,
-                                                  uint16_t *__restrict__ wbf, float *__restrict__ bm) {
+                                                  uint16_t *__restrict__ wbf, uint16_t *__restrict__ wx6,
+                                                  float *__restrict__ bm) {
     const long long WW = (long long)W * W, total = (long long)n_mid * WW;
     const long long mid0 = 4LL * W;  // W0 and b0 come first
     const int KB = W / 64;
@@ -39,8 +51,14 @@ __global__ void __launch_bounds__(256) k_prep_mlp(const float *__restrict__ para
         wtb[l * WW + (long long)o * W + perm_pos(i)] = v;
         const int kb = i >> 6, kk = i & 63;
         const int byte = (o >> 3) * 1024 + (o & 7) * 128 + (((kk >> 3) ^ (o & 7)) << 4) + (kk & 7) * 2;
-        const uint32_t u = __float_as_uint(v);
-        wbf[((long long)l * KB + kb) * W * 64 + byte / 2] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+        const uint16_t hi = bf16_rne(v);
+        wbf[((long long)l * KB + kb) * W * 64 + byte / 2] = hi;
+        const float rem = v - bf16_val(hi);  // exact
+        const uint16_t mid = bf16_rne(rem);
+        const uint16_t low = bf16_rne(rem - bf16_val(mid));
+        const uint16_t parts[3] = {low, mid, hi};
+        for (int p = 0; p < 3; ++p)
+            wx6[(((long long)l * 3 + p) * KB + kb) * W * 64 + byte / 2] = parts[p];
     }
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n_mid * W;
          e += (long long)gridDim.x * blockDim.x) {
@@ -51,9 +69,9 @@ __global__ void __launch_bounds__(256) k_prep_mlp(const float *__restrict__ para
 
 }  // namespace
 
-void launch_prep_mlp(const float *params, int W, int n_mid, float *wt, float *wtb, uint16_t *wbf, float *bm,
-                     cudaStream_t st) {
-    k_prep_mlp<<<1024, 256, 0, st>>>(params, W, n_mid, wt, wtb, wbf, bm);
+void launch_prep_mlp(const float *params, int W, int n_mid, float *wt, float *wtb, uint16_t *wbf, uint16_t *wx6,
+                     float *bm, cudaStream_t st) {
+    k_prep_mlp<<<1024, 256, 0, st>>>(params, W, n_mid, wt, wtb, wbf, wx6, bm);
 }
 
 }  // namespace gh

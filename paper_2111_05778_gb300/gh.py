@@ -17,9 +17,9 @@ from . import _buildlib
 
 GH_OK, GH_ERR_ARG, GH_ERR_CAPACITY, GH_ERR_CUDA, GH_ERR_NONFINITE, GH_ERR_UNIMPLEMENTED, GH_ERR_DEVICE = range(7)
 GH_SDB_CSG, GH_SDB_MLP = 0, 1
-GH_FP32, GH_BF16_REFINE = 0, 1
+GH_FP32, GH_BF16_REFINE, GH_BF16_REFINE_X6 = 0, 1, 2
 GH_TAU_DIAGONAL, GH_TAU_HALF_DIAGONAL = 0, 1
-PRECISIONS = {"fp32": GH_FP32, "bf16": GH_BF16_REFINE, "bf16_refine": GH_BF16_REFINE}
+PRECISIONS = {"fp32": GH_FP32, "bf16": GH_BF16_REFINE, "bf16_refine": GH_BF16_REFINE, "bf16x6": GH_BF16_REFINE_X6}
 GH_METHOD_HOP, GH_METHOD_ENUM = 0, 1
 METHODS = {"hop": GH_METHOD_HOP, "enum": GH_METHOD_ENUM}
 

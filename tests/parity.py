@@ -2,7 +2,8 @@
 
 The FP32 path against the FP64 oracle:
 * Excluded cells.  A cell is left out of the exact comparison only when one
-  of its corners (a) has |f64| < 1e-6 h (the tie band the workloads state), or
+  of its corners (a) has |f64| < 1e-6 h (the tie band the workloads state;
+  corners where f is zero up to FP64 rounding are counted apart), or
   (b) has a GPU FP32 value whose sign differs from the FP64 sign.  (b) is
   measured, not assumed: the GPU's own FP32 evaluator (gh_eval, the evaluator
   the hopper and the vertex pass use, bit for bit) is run at the corner
@@ -107,15 +108,17 @@ def tri_cells(keys, N):
     return out
 
 
-def gpu_fp32(gsdb):
-    """Callable: float32 points [n,3] -> the GPU's FP32 values (float64)."""
+def gpu_fp32(gsdb, precision="fp32"):
+    """Callable: float32 points [n,3] -> the GPU's values (float64) from the
+    evaluator that produced the mesh's corner values: FP32 (plain and BF16 +
+    FP32 refinement) or the split-BF16 engine ("bf16x6" refinement)."""
     import torch
 
     from paper_2111_05778_gb300 import gh
 
     def f(p32):
         p = torch.from_numpy(np.ascontiguousarray(p32, np.float32).reshape(-1, 3)).cuda()
-        return gh.eval_points(gsdb, p, "fp32").cpu().numpy().astype(np.float64)
+        return gh.eval_points(gsdb, p, precision).cpu().numpy().astype(np.float64)
 
     return f
 
@@ -126,10 +129,12 @@ def _rows(a):
 
 
 def compare(gpu, osdb, N, lo=-1.0, hi=1.0, ref=None, restrict_cells=None, gsdb=None, min_bare=0.999,
-            max_excluded=None, check=True, f32=None):
+            max_excluded=None, check=True, f32=None, gprec="fp32"):
     """gpu: gh.Mesh with keys and cells; osdb: the oracle SDB; ref: oracle
     Result with the oracle's sign-change cells (cells/cases) and triangles;
-    gsdb: the GPU SDB (its FP32 evaluator decides (b) above and delta32).
+    gsdb: the GPU SDB (its FP32 evaluator decides (b) above and delta32;
+    gprec="bf16x6" takes its split-BF16 evaluator instead, the one that
+    refines the corners of that precision's meshes).
     restrict_cells: optional predicate (cell ids -> bool mask) limiting the
     comparison to a sampled region.  max_excluded: bound on tie + sign-flip
     cells (default max(32, 0.2 % of the compared cells)).  Returns a dict of
@@ -137,7 +142,7 @@ def compare(gpu, osdb, N, lo=-1.0, hi=1.0, ref=None, restrict_cells=None, gsdb=N
     (mismatch counts included).  f32: optional callable standing in for the
     GPU's FP32 evaluator (float32 points -> values), for CPU self-tests."""
     assert gsdb is not None or f32 is not None, "compare() needs the GPU SDB for its FP32 corner values"
-    f32_eval = f32 if f32 is not None else gpu_fp32(gsdb)
+    f32_eval = f32 if f32 is not None else gpu_fp32(gsdb, "bf16x6" if gprec == "bf16x6" else "fp32")
     h = (hi - lo) / N
     tie = TIE_H * h
     gc = gpu.cell_ids.cpu().numpy().astype(np.int64)
@@ -164,7 +169,12 @@ def compare(gpu, osdb, N, lo=-1.0, hi=1.0, ref=None, restrict_cells=None, gsdb=N
     delta32 = 2.0 * float(np.abs(f32 - f64).max()) if f64.size else 0.0
     in_band = (np.abs(f64) < tie).any(1)
     flipped = ((f32 < 0) != (f64 < 0)).any(1) & ~in_band
+    # corners where f is zero up to FP64 rounding: the tie rule's own cases
+    # (f = 0 counts as outside), which a lattice aligned with the scene's
+    # centres and radii can produce by the hundred; not bounded by max_excluded
+    exact = (np.abs(f64) < 1e-13).any(1)
     excl = allc[in_band | flipped]
+    n_bounded = int(((in_band & ~exact) | flipped).sum())
     limit = max_excluded if max_excluded is not None else max(32, int(0.002 * allc.size))
     gset = np.setdiff1d(gc, excl)
     oset = np.setdiff1d(oc, excl)
@@ -195,15 +205,17 @@ def compare(gpu, osdb, N, lo=-1.0, hi=1.0, ref=None, restrict_cells=None, gsdb=N
     err = np.abs(p_g[ig] - p_o[io]).max(1) if kk.size else np.zeros(0)
     tol = 1e-4 * h + h * delta32 / np.maximum(np.abs(fA - fB), 1e-300)
     bare = float(np.mean(err <= 1e-4 * h)) if err.size else 1.0
-    st = {"cells": int(gset.size), "tie_cells": int(in_band.sum()), "sign_flip_cells": int(flipped.sum()),
+    st = {"cells": int(gset.size), "tie_cells": int(in_band.sum()), "exact_zero_cells": int(exact.sum()),
+          "sign_flip_cells": int(flipped.sum()),
           "mismatched_cells": int(np.setdiff1d(gset, oset).size + np.setdiff1d(oset, gset).size + len(bad_case)),
           "mismatched_tris": tri_mismatch, "delta32": delta32, "tris": int(ct_g.shape[0]), "verts": int(kk.size),
           "vertices_over_tol": int((err > tol).sum()),
           "max_err_over_h": float(err.max() / h) if err.size else 0.0, "bare_frac": bare}
     if check:
         try:
-            assert excl.size <= limit, "%d cells excluded (%d in the 1e-6 h band, %d FP32 sign flips) > %d" % (
-                excl.size, st["tie_cells"], st["sign_flip_cells"], limit)
+            assert n_bounded <= limit, "%d cells excluded (%d in the 1e-6 h band, %d of them exact zeros; " \
+                "%d FP32 sign flips) > %d" % (n_bounded, st["tie_cells"], st["exact_zero_cells"],
+                                               st["sign_flip_cells"], limit)
             assert gset.size == oset.size and (gset == oset).all(), (
                 "surface cells differ: %d only on GPU, %d only in oracle" % (np.setdiff1d(gset, oset).size,
                                                                              np.setdiff1d(oset, gset).size))

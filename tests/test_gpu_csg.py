@@ -52,7 +52,9 @@ def test_ragged_and_offset_grids(N, lo, hi):
     o = oracle.csg(prims)
     ref = oracle.enum(o, N, lo, hi)
     st = parity.compare(m, o, N, lo, hi, ref=ref, gsdb=sdb)
-    assert st["tie_cells"] + st["sign_flip_cells"] <= 8
+    # lattices aligned with the scene put corners exactly on the surface (f = 0
+    # up to FP64 rounding); every other excluded cell is bounded
+    assert st["tie_cells"] - st["exact_zero_cells"] + st["sign_flip_cells"] <= 8
 
 
 @pytest.mark.parametrize("tau_mode", [0, 1])

@@ -1,0 +1,47 @@
+"""The split-BF16 tensor-core evaluator ("x6": each FP32 operand split into
+three BF16 parts, six part products accumulated in FP32) against the FP64
+oracle and against plain FP32, and the BF16 path refined with it
+(GH_BF16_REFINE_X6) against the oracle.  It may replace FP32 refinement
+only with an error against FP64 no larger than plain FP32's."""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2111_05778_gb300 import gh, synth  # noqa: E402
+
+
+def _pair(seed, width):
+    p = synth.mlp_params(seed, width)
+    return gh.MlpSdb(p, width), oracle.mlp(width, synth.MLP_NMID, p.astype(np.float64))
+
+
+@pytest.mark.parametrize("width", [64, 128, 256])
+def test_x6_error_no_larger_than_fp32(width):
+    sdb, o = _pair(1, width)
+    n = (1 << 20) + 77  # 2^20 points and a ragged tail
+    P = torch.from_numpy(synth.uniform_points(12, n)).cuda()
+    ref = o.eval_many(P.cpu().numpy().astype(np.float64))
+    f32 = gh.eval_points(sdb, P, "fp32").cpu().numpy().astype(np.float64)
+    fx6 = gh.eval_points(sdb, P, "bf16x6").cpu().numpy().astype(np.float64)
+    e32, ex6 = np.abs(f32 - ref), np.abs(fx6 - ref)
+    print("width %d: max |f32 - f64| %.3g (mean %.3g), max |x6 - f64| %.3g (mean %.3g)" % (
+        width, e32.max(), e32.mean(), ex6.max(), ex6.mean()))
+    assert ex6.max() <= e32.max()
+    assert ex6.mean() <= e32.mean()
+
+
+@pytest.mark.parametrize("width,N", [(64, 40), (128, 48), (256, 64)])
+def test_bf16_x6_refine_full(width, N):
+    sdb, o = _pair(1 + width, width)
+    eps = sdb.calibrate(N)
+    m = gh.polygonize(sdb, N, precision="bf16x6", eps=eps, keys=True, cells=True)
+    st = parity.compare(m, o, N, ref=oracle.enum(o, N), gsdb=sdb, gprec="bf16x6")
+    print("x6 refine width %d N %d: %s" % (width, N, st))
+    assert st["cells"] > 1000
+    assert m.stats["refined_vertices"] > 0
+    assert st["tie_cells"] + st["sign_flip_cells"] <= 8
