@@ -9,6 +9,7 @@
 
 namespace gh {
 namespace tc {
+namespace {  // internal linkage: every translation unit gets its own copy
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // limit of every bounded wait
 constexpr int CTL_ABORT = 2;                            // ctl bit: a wait timed out, every role leaves
@@ -175,5 +176,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+}  // namespace
 }  // namespace tc
 }  // namespace gh
