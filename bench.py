@@ -181,7 +181,8 @@ def _parity():
 def _acc(st, N, stats=None):
     """The accuracy record of one comparison (parity.compare, reporting form)."""
     out = {"cells_compared": st["cells"], "tie_cells_1e-6h": st["tie_cells"],
-           "fp32_sign_flip_cells": st["sign_flip_cells"], "mismatched_cells": st["mismatched_cells"],
+           "exact_zero_cells": st["exact_zero_cells"], "fp32_sign_flip_cells": st["sign_flip_cells"],
+           "mismatched_cells": st["mismatched_cells"],
            "mismatched_triangles": st["mismatched_tris"], "vertices_compared": st["verts"],
            "vertices_over_tolerance": st["vertices_over_tol"], "max_vertex_err_over_h": st["max_err_over_h"],
            "share_within_1e-4h": st["bare_frac"], "delta32": st["delta32"]}

