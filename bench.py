@@ -182,6 +182,7 @@ def _acc(st, N, stats=None):
     """The accuracy record of one comparison (parity.compare, reporting form)."""
     out = {"cells_compared": st["cells"], "tie_cells_1e-6h": st["tie_cells"],
            "exact_zero_cells": st["exact_zero_cells"], "fp32_sign_flip_cells": st["sign_flip_cells"],
+           "fp32_sign_flip_cells_outside_band": st["sign_flip_outside_band"],
            "mismatched_cells": st["mismatched_cells"],
            "mismatched_triangles": st["mismatched_tris"], "vertices_compared": st["verts"],
            "vertices_over_tolerance": st["vertices_over_tol"], "max_vertex_err_over_h": st["max_err_over_h"],

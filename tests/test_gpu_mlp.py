@@ -32,7 +32,7 @@ def test_mlp_fp32_full(width, N):
     ref = oracle.enum(o, N)
     st = parity.compare(m, o, N, ref=ref, gsdb=sdb)
     assert st["cells"] > 1000
-    assert st["sign_flip_cells"] <= 8
+    assert st["sign_flip_outside_band"] <= 8
 
 
 def test_enumeration_equals_hopping_mlp():
