@@ -395,7 +395,7 @@ def run_ours(args):
     sdb = gh.MlpSdb(params, W)
     precision = args.precision
     if precision == "auto":
-        precision = "bf16" if _bf16_available(sdb) else "fp32"
+        precision = "bf16x6" if _bf16_available(sdb) else "fp32"
     eps = None
     if precision in ("bf16", "bf16x6"):
         eps = sdb.calibrate(N)
@@ -481,7 +481,9 @@ def run_ours(args):
     ctx = {}
     if precision != "fp32":
         line["fp32_path"] = companion(gh, torch, sdb, N, bufs, stream, flush, "fp32")
-        line["bf16x6_refine_path"] = companion(gh, torch, sdb, N, bufs, stream, flush, "bf16x6", eps)
+        other = "bf16" if precision == "bf16x6" else "bf16x6"
+        line["bf16_fp32_refine_path" if other == "bf16" else "bf16x6_refine_path"] = companion(
+            gh, torch, sdb, N, bufs, stream, flush, other, eps)
     solo = rank == 0 and world == 1
     if solo and not args.no_cpu_baseline:
         meshes = {precision: gh.polygonize(sdb, N, precision=precision, eps=eps, keys=True, cells=True)}
@@ -751,7 +753,7 @@ def work_c3(args, flush, stream):
         Ns.append(N)
         prims_of.append(p)
     setup_s = time.perf_counter() - t0
-    precision = "bf16" if args.precision == "auto" else args.precision
+    precision = "bf16x6" if args.precision == "auto" else args.precision
     rb, mt, timings = tune.tune_batch(sdbs, Ns, precision=precision, use_cache=False)
     base = gh.polygonize_batch(sdbs, Ns, precision=precision, ray_block=rb, mlp_tiles=mt)
     caps = [int(c * 1.05) + 4096 for c in base.counts()]
@@ -822,10 +824,12 @@ def work_c4(args, flush, stream):
     return rec, {"verts": verts, "dldv": dldv, "grad": grad, "params": params, "W": W}
 def run_crossover(args):
     """Grid hopping against enumeration (Sec. 2: every lattice point and cell)
-    on the same GPU, for the analytic scene, the width-256 network and a
-    network of the paper's own architecture (8 layers of width 64, batch
-    normalisation folded, lambda = 1.5), over N (the paper's Sec. 5
-    comparisons, here with both methods on the GB300)."""
+    and, for the analytic scene, continuation (Sec. 2: the surface crawled
+    from seed points, here one left of every primitive's centre) on the same
+    GPU, for the analytic scene, the width-256 network and a network of the
+    paper's own architecture (8 layers of width 64, batch normalisation
+    folded, lambda = 1.5), over N (the paper's Sec. 5 comparisons, here with
+    every method on the GB300)."""
     import torch
 
     from paper_2111_05778_gb300 import gh, synth
@@ -844,6 +848,17 @@ def run_crossover(args):
             variants = [("hop_fp32", "fp32", "hop"), ("enum_fp32", "fp32", "enum")]
             if name != "csg":
                 variants.insert(1, ("hop_bf16", "bf16", "hop"))
+            if name == "csg":
+                seeds = synth.csg_prims(0)[:, 2:5].copy()
+                seeds[:, 0] -= 0.3
+                probe = gh.polygonize_cont(sdb, N, seeds)
+                bufs = gh.Buffers(int(probe.n_tris * 1.05) + 4096)
+                gh.polygonize_cont_into(sdb, N, seeds, bufs)
+                res["cont_fp32_ms"] = _timed(lambda: gh.polygonize_cont_into(sdb, N, seeds, bufs, sync=False,
+                                                                             stream=stream),
+                                             max(1, args.steps // 2), 1, flush, stream)
+                res["cont_fp32_evals"] = bufs.stats_dict()["hop_evals"]
+                res["cont_surface_cells"] = bufs.stats_dict()["surface_cells"]
             for key, prec, meth in variants:
                 eps = sdb.calibrate(N, n_points=1 << 18) if prec == "bf16" else None
                 probe = gh.polygonize(sdb, N, precision=prec, eps=eps, method=meth)

@@ -314,6 +314,24 @@ int gh_batch_graph_free(void *graph);
 int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim *prims, int32_t n_prim, int32_t tau_mode,
                               gh_mesh *out, void *stream);
 
+/* Continuation (Sec. 2, the comparison method of Sec. 5.1) for analytic
+ * SDBs: the surface is crawled from seed cells instead of hopped.  For each
+ * seed point (host float32 seeds[n_seeds][3], 1 <= n_seeds <= 65536) the cell
+ * holding it is found, and the lattice vertices of its (j, k) line are scanned
+ * in +x order from there: the first sign change gives the seed cell (none
+ * when the line has none).  From the seed cells, every cell whose surface
+ * crosses a face into a neighbour adds that neighbour (each cell once), and
+ * each cell gets Marching Cubes from its own eight corner values -- the
+ * evaluator and lattice points of gh_polygonize, so a crawled component's
+ * triangles equal gh_polygonize's bit for bit.  Each seed reaches one
+ * connected component of the mesh (seeds of one component add nothing).
+ * opts: precision GH_FP32 (the only one); sync and the capacity protocol as
+ * gh_polygonize; stats->hop_evals counts the evaluations (8 per crawled cell
+ * plus the seed searches), marked_cells the crawled cells.  No indexed mesh.
+ * Errors: GH_ERR_UNIMPLEMENTED for a neural SDB, others as gh_polygonize. */
+int gh_polygonize_cont(const gh_grid *grid, const gh_sdb *sdb, const float *seeds, int32_t n_seeds,
+                       const gh_options *opts, gh_mesh *out, void *stream);
+
 /* The order in which the hoppers take the N^2 columns (a column is i*N + j,
  * i along x, j along y): the c-th claim of the queue gets column
  * gh_column_order(N, c).  Square rings around the grid centre, innermost

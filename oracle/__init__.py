@@ -67,6 +67,8 @@ def lib():
             L.or_enum.restype = P
             L.or_enum.argtypes = [P, I, P, D, I, I]
             L.or_hop.restype = P
+            L.or_cont.restype = P
+            L.or_cont.argtypes = [P, I, P, D, I64, P]
             L.or_hop.argtypes = [P, I, P, D, D, D, I64, P]
             L.or_res_count.restype = I64
             L.or_res_count.argtypes = [P, I]
@@ -288,6 +290,15 @@ def hop(sdb: SDB, N, lo=-1.0, hi=1.0, tau_mode=TAU_DIAGONAL, eps=0.0, cols=None)
         return Result(lib().or_hop(sdb.h, N, _ptr(lo3), h, tau, float(eps), 0, None))
     c = np.ascontiguousarray(cols, dtype=np.int64).ravel()
     return Result(lib().or_hop(sdb.h, N, _ptr(lo3), h, tau, float(eps), c.size, _ptr(c)))
+
+
+def cont(sdb: SDB, N, seeds, lo=-1.0, hi=1.0) -> Result:
+    """Continuation (Sec. 2): the surface crawled from seed points (cells of
+    each seed's component, in visit order, with their triangles); col_evals
+    holds each seed's cell id or -1."""
+    lo3, h = _lo_h(N, lo, hi)
+    sp = np.ascontiguousarray(seeds, dtype=np.float64).reshape(-1, 3)
+    return Result(lib().or_cont(sdb.h, N, _ptr(lo3), h, sp.shape[0], _ptr(sp)))
 
 
 def polygonize(sdb: SDB, N, lo=-1.0, hi=1.0, tau_mode=TAU_DIAGONAL, cols=None):

@@ -1038,3 +1038,89 @@ void or_set_threads(int n) {
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Continuation (Sec. 2): crawl the surface from seed cells                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * The comparison method of Sec. 2 and 5.1: starting from a seed cell that
+ * the surface passes through, cells are propagated across the surface until
+ * the surface is closed; each seed gives (at most) one mesh component.  A
+ * cell's surface leaves it through exactly the faces whose four corners do
+ * not all have one sign, so the neighbour across each such face is a surface
+ * cell too and joins the queue (breadth first, each cell once).
+ * Seeds are points: from the cell (i0, j0, k0) holding the point, the lattice
+ * vertices (a, j0, k0), a = i0 .. N, are scanned in +x order and the first
+ * pair with a sign change gives the seed cell (a, j0, k0) (Bloomenthal's
+ * search for a seed from a point); a point whose line has no sign change
+ * gives none.
+ * Result: R_CELL / R_CASE the visited cells in visit order, the triangles of
+ * each (Marching Cubes as in or_mc), R_COLEVAL one entry per seed: the seed
+ * cell id or -1.
+ */
+static double corner_val(const osdb *s, const ogrid *g, int64_t a, int64_t b, int64_t c) {
+    double p[3] = {g->lo[0] + (double)a * g->h, g->lo[1] + (double)b * g->h, g->lo[2] + (double)c * g->h};
+    return sdb_eval(s, p);
+}
+
+void *or_cont(const void *hs, int N, const double *lo, double h, int64_t nseeds, const double *seeds) {
+    const osdb *s = (const osdb *)hs;
+    ogrid g;
+    if (grid_of(&g, N, lo, h)) return NULL;
+    ensure_table();
+    ores *out = ores_new();
+    const int64_t NN = N, ncell = NN * NN * NN;
+    uint64_t *vis = (uint64_t *)calloc((size_t)(ncell / 64 + 1), sizeof(uint64_t));
+    ovec q = {0, 0, 8, NULL};
+    for (int64_t sd = 0; sd < nseeds; ++sd) {
+        int64_t ijk[3], found = -1;
+        for (int a = 0; a < 3; ++a) {
+            double x = floor((seeds[3 * sd + a] - g.lo[a]) / g.h);
+            ijk[a] = x < 0 ? 0 : (x > NN - 1 ? NN - 1 : (int64_t)x);
+        }
+        double fprev = corner_val(s, &g, ijk[0], ijk[1], ijk[2]);
+        for (int64_t a = ijk[0]; a < NN; ++a) {
+            double fnext = corner_val(s, &g, a + 1, ijk[1], ijk[2]);
+            if ((fprev < 0) != (fnext < 0)) {
+                found = (a * NN + ijk[1]) * NN + ijk[2];
+                break;
+            }
+            fprev = fnext;
+        }
+        ov_push(&out->v[R_COLEVAL], &found);
+        if (found >= 0 && !(vis[found >> 6] >> (found & 63) & 1)) {
+            vis[found >> 6] |= 1ull << (found & 63);
+            ov_push(&q, &found);
+        }
+    }
+    for (int64_t head = 0; head < q.n; ++head) {
+        int64_t c = ((int64_t *)q.p)[head];
+        int64_t k = c % NN, j = (c / NN) % NN, i = c / (NN * NN);
+        double fv[8];
+        for (int b = 0; b < 8; ++b) {
+            int x[3];
+            corner_xyz(b, x);
+            fv[b] = corner_val(s, &g, i + x[0], j + x[1], k + x[2]);
+        }
+        int32_t cs = mc_cell(s, &g, i, j, k, out);
+        ov_push(&out->v[R_CELL], &c);
+        ov_push(&out->v[R_CASE], &cs);
+        for (int ax = 0; ax < 3; ++ax)
+            for (int side = 0; side < 2; ++side) {
+                int neg = 0;
+                for (int b = 0; b < 8; ++b)
+                    if (((b >> ax) & 1) == side) neg += fv[b] < 0;
+                if (neg == 0 || neg == 4) continue; /* the surface does not cross this face */
+                int64_t n3[3] = {i, j, k};
+                n3[ax] += side ? 1 : -1;
+                if (n3[ax] < 0 || n3[ax] >= NN) continue;
+                int64_t nc = (n3[0] * NN + n3[1]) * NN + n3[2];
+                if (vis[nc >> 6] >> (nc & 63) & 1) continue;
+                vis[nc >> 6] |= 1ull << (nc & 63);
+                ov_push(&q, &nc);
+            }
+    }
+    free(q.p);
+    free(vis);
+    return out;
+}

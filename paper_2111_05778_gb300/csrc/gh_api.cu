@@ -226,6 +226,8 @@ struct gh_sdb {
     Scratch scr{};
     int scr_N = 0;
     float *adj = nullptr;  // adjoint work buffer
+    float *seeds = nullptr;  // continuation: seed points on the device
+    int cap_seeds = 0;
     size_t adj_floats = 0;
     Item h_item{};           // descriptor of the last single call (host copy)
     Item *d_item = nullptr;  // and on the device
@@ -374,7 +376,7 @@ extern "C" int gh_release_cache(void) {
         cudaSetDevice(e.device);
         Scratch &c = e.scr;
         void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                        c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum};
+                        c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.cidx, c.vis};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -412,7 +414,7 @@ extern "C" int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out) {
 static void free_scratch(gh_sdb *s) {
     Scratch &c = s->scr;
     void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum};
+                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.cidx, c.vis};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->scr = Scratch{};
@@ -431,6 +433,7 @@ extern "C" int gh_destroy_sdb(gh_sdb *s) {
     }
     free_scratch(s);
     if (s->adj) cudaFree(s->adj);
+    if (s->seeds) cudaFree(s->seeds);
     if (s->d_item) cudaFree(s->d_item);
     for (void *p : s->dbufs) cudaFree(p);
     delete s;
@@ -461,15 +464,21 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     long long cv = c.cap_verts > want_verts ? c.cap_verts : want_verts;
     float *keep_lat = c.lat;
     const long long keep_cap = c.cap_lat;
+    uint32_t *keep_vis = c.vis;
+    const long long keep_vcap = c.cap_vis;
     c.lat = nullptr;
+    c.vis = nullptr;
     free_scratch(s);
     c.lat = keep_lat;
     c.cap_lat = keep_cap;
+    c.vis = keep_vis;
+    c.cap_vis = keep_vcap;
     s->item_valid = false;
     const long long ncols = (long long)NN * NN, nlines = (long long)(NN + 1) * (NN + 1);
     GH_CUDA(cudaMalloc((void **)&c.ctr, sizeof(Counters)));
     GH_CUDA(cudaMalloc((void **)&c.marks_raw, sizeof(unsigned long long) * cm));
     GH_CUDA(cudaMalloc((void **)&c.marks_csr, sizeof(unsigned long long) * cm));
+    GH_CUDA(cudaMalloc((void **)&c.cidx, sizeof(uint32_t) * 4 * cm));
     GH_CUDA(cudaMalloc((void **)&c.colcount, sizeof(uint32_t) * ncols));
     GH_CUDA(cudaMalloc((void **)&c.coloff, sizeof(uint32_t) * (ncols + 1)));
     GH_CUDA(cudaMalloc((void **)&c.linecount, sizeof(uint32_t) * nlines));
@@ -745,6 +754,80 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         if (out->vert_xyz && c.mesh_verts > (unsigned long long)out->capacity_verts)
             return fail(GH_ERR_CAPACITY, "vertex buffer holds %lld, %llu needed", (long long)out->capacity_verts,
                         c.mesh_verts);
+        return GH_OK;
+    }
+    return fail(GH_ERR_CAPACITY, "internal scratch kept overflowing");
+}
+
+// The visited bits of the continuation method (N^3 bits).
+static int ensure_vis(gh_sdb *s, int N) {
+    const long long need = ((long long)N * N * N + 31) / 32;
+    if (s->scr.cap_vis >= need) return GH_OK;
+    if (s->scr.vis) cudaFree(s->scr.vis);
+    s->scr.vis = nullptr;
+    s->scr.cap_vis = 0;
+    GH_CUDA(cudaMalloc((void **)&s->scr.vis, sizeof(uint32_t) * need));
+    s->scr.cap_vis = need;
+    s->item_valid = false;
+    return GH_OK;
+}
+
+extern "C" int gh_polygonize_cont(const gh_grid *grid, const gh_sdb *csdb, const float *seeds, int32_t n_seeds,
+                                  const gh_options *opts, gh_mesh *out, void *stream) {
+    gh_sdb *s = const_cast<gh_sdb *>(csdb);
+    if (!s) return fail(GH_ERR_ARG, "NULL sdb");
+    gh_options o{GH_FP32, GH_TAU_DIAGONAL, -1.f, 1, 0, 0, GH_METHOD_HOP};
+    if (opts) o = *opts;
+    GridP g;
+    int rc = check_grid(grid, &g, GH_TAU_DIAGONAL);
+    if (rc) return rc;
+    if ((rc = check_mesh(out))) return rc;
+    if (!seeds || n_seeds < 1 || n_seeds > 65536) return fail(GH_ERR_ARG, "continuation: 1..65536 seed points needed");
+    for (int i = 0; i < 3 * n_seeds; ++i)
+        if (!isfinite(seeds[i])) return fail(GH_ERR_ARG, "continuation: seed point %d is not finite", i / 3);
+    if (s->kind != GH_SDB_CSG) return fail(GH_ERR_UNIMPLEMENTED, "continuation runs on analytic SDBs only");
+    if (o.precision != GH_FP32) return fail(GH_ERR_UNIMPLEMENTED, "continuation runs in FP32 only");
+    if (wants_index(*out)) return fail(GH_ERR_UNIMPLEMENTED, "continuation: no indexed mesh output");
+    int dev, nsm;
+    if ((rc = ensure_device(&dev, &nsm))) return rc;
+    if (dev != s->device) return fail(GH_ERR_ARG, "SDB lives on device %d, current device is %d", s->device, dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->cap_seeds < n_seeds) {
+        if (s->seeds) cudaFree(s->seeds);
+        s->seeds = nullptr;
+        s->cap_seeds = 0;
+        GH_CUDA(cudaMalloc((void **)&s->seeds, sizeof(float) * 3 * n_seeds));
+        s->cap_seeds = n_seeds;
+    }
+    const long long N2 = (long long)g.N * g.N;
+    long long want_m = 8 * N2 > (1 << 16) ? 8 * N2 : (1 << 16);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((rc = ensure_scratch(s, g.N, want_m, 2 * want_m)) || (rc = ensure_vis(s, g.N))) return rc;
+        Scratch &c = s->scr;
+        GH_CUDA(cudaMemcpyAsync(s->seeds, seeds, sizeof(float) * 3 * n_seeds, cudaMemcpyHostToDevice, st));
+        launch_init(c, st);
+        launch_cont_csg(s->d_prims, s->nprim, g, c, s->seeds, n_seeds, *out, nsm, st);
+        launch_finalize(c, *out, N2, st);
+        g_prof.recorded = false;
+        g_prof.launches = 5;
+        GH_CUDA(cudaGetLastError());
+        if (!o.sync) return GH_OK;
+        Counters h;
+        GH_CUDA(cudaMemcpyAsync(&h, c.ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+        GH_CUDA(cudaStreamSynchronize(st));
+        if (h.flags & FLAG_MARK_OVERFLOW) {
+            want_m = (long long)(h.marks + h.marks / 4 + 1024);
+            continue;
+        }
+        if (h.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
+        if (h.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
+        if (h.tris > (unsigned long long)out->capacity_tris)
+            return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris,
+                        h.tris);
+        if (out->cell_ids && h.cells > (unsigned long long)out->capacity_cells)
+            return fail(GH_ERR_CAPACITY, "cell buffer holds %lld, %llu needed", (long long)out->capacity_cells,
+                        h.cells);
         return GH_OK;
     }
     return fail(GH_ERR_CAPACITY, "internal scratch kept overflowing");
@@ -1222,12 +1305,15 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     off += up256(4 * (nlines + 1));
     c.blocksum = (uint32_t *)(q + off);
     off += up256(4 * 4096);
-    const size_t per = 2 * 8 + 2 * (8 + 4);  // marks raw + grouped, two vertices (key + value) per mark
+    // marks raw + grouped + their corner indices, two vertices (key + value) per mark
+    const size_t per = 2 * 8 + 16 + 2 * (8 + 4);
     const size_t M = ((GH_NOALLOC_SCRATCH_BYTES - off - 4 * 256) / per) & ~(size_t)255;
     c.marks_raw = (unsigned long long *)(q + off);
     off += up256(8 * M);
     c.marks_csr = (unsigned long long *)(q + off);
     off += up256(8 * M);
+    c.cidx = (uint32_t *)(q + off);
+    off += up256(16 * M);
     c.vkey = (unsigned long long *)(q + off);
     off += up256(8 * 2 * M);
     c.vval = (float *)(q + off);

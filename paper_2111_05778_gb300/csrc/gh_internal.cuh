@@ -23,7 +23,9 @@ struct Counters {
     unsigned long long next_tile2; // second work counter (refinement pass)
     unsigned long long row_slots;  // rows the neural hopper ran (live or not): 128 per tile-step
     unsigned long long mesh_verts; // indexed output: crossing lattice edges
-    unsigned long long pad[4];
+    unsigned long long q_head;     // continuation: next queue slot to take
+    unsigned long long q_pending;  // continuation: cells queued and not yet finished
+    unsigned long long pad[2];
 };
 
 enum : unsigned long long {
@@ -158,6 +160,8 @@ struct Scratch {
     uint32_t *lineoff;              // [(N+1)^2 + 1]
     uint32_t *blocksum;             // scan partials
     unsigned long long *vkey;       // line | c << 32, grouped by line, c ascending
+    uint32_t *cidx;                 // [cap_marks][4]: vertex-list index of corner (q, c = k) of each
+                                    // grouped mark not proven empty, q = ox + 2 oy
     float *vval;                    // [cap_verts]
     uint8_t *vflag;                 // [cap_verts] refinement flags
     uint32_t *rlist;                // [cap_verts] vertices to refine
@@ -167,6 +171,8 @@ struct Scratch {
     uint32_t *ebase;                // indexed output: first mesh vertex of each list entry [cap_verts + 1]
     uint32_t *ebsum;                // its scan partials
     long long cap_index;            // entries ebase was sized for (0: none)
+    uint32_t *vis;                  // continuation: visited bit per cell [N^3 / 32 words]
+    long long cap_vis;              // words of vis
 };
 
 // One polygonization of a batch: grid, scratch and SDB.  Kernels that serve
@@ -214,6 +220,10 @@ void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s
 void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
 void launch_enum_stats(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st);
+// continuation (Sec. 2) for analytic SDBs: seed search from host-given points
+// (seeds: device [n][3]) and the surface crawl with Marching Cubes per cell
+void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, const float *seeds, int n_seeds,
+                     const gh_mesh &out, int nsm, cudaStream_t st);
 void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long long n, float *out,
                             cudaStream_t st);
 

@@ -489,7 +489,8 @@ __global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
             for (int w = 0; w < NW; ++w) cnt += (uint32_t)__popc(bits[w * LINES_T]);
             s.linecount[line] = cnt;
         } else {
-            unsigned long long o = s.lineoff[line];
+            const uint32_t lbase = s.lineoff[line];
+            unsigned long long o = lbase;
             for (int w = 0; w < NW; ++w) {
                 uint32_t v = bits[w * LINES_T];
                 while (v) {
@@ -499,6 +500,25 @@ __global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
                     ++o;
                 }
             }
+            // the list index of vertex (line, k) for every mark of the four
+            // columns around the line: the rank of bit k in the line's set (the
+            // marks of a column come in ascending k, so one pass over the words)
+            for (int di = -1; di <= 0; ++di)
+                for (int dj = -1; dj <= 0; ++dj) {
+                    const int i = a + di, j = b + dj;
+                    if (i < 0 || j < 0 || i >= N || j >= N) continue;
+                    const uint32_t q = (uint32_t)(-di) + 2u * (uint32_t)(-dj);
+                    const uint32_t col = (uint32_t)i * N + j;
+                    int w = 0;
+                    uint32_t below = 0;
+                    for (uint32_t m = off[col], e = off[col + 1]; m < e; ++m) {
+                        const unsigned long long r = __ldg(mk + m);
+                        if (mark_empty(r)) continue;
+                        const uint32_t k = mark_k(r);
+                        for (; w < (int)(k >> 5); ++w) below += (uint32_t)__popc(bits[w * LINES_T]);
+                        s.cidx[4ull * m + q] = lbase + below + (uint32_t)__popc(bits[w * LINES_T] & ((1u << (k & 31)) - 1u));
+                    }
+                }
         }
     }
 }
@@ -577,20 +597,18 @@ void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long l
 // ---------------------------------------------------------------------------
 // 5. Marching Cubes on the marked cells.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t find_c(const unsigned long long *__restrict__ vkey, uint32_t lo, uint32_t hi,
-                                           uint32_t c) {
-    // vkey[lo..hi) has ascending c (upper 32 bits); c is present by construction
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if ((uint32_t)(vkey[mid] >> 32) <= c) lo = mid; else hi = mid;
-    }
-    return lo;
-}
+// Triangles a warp stages in shared memory before writing them out: at most
+// 5 per cell, 32 cells, 9 floats each.
+constexpr int EMIT_STAGE = 32 * 5 * 9;
 
 // Case index, triangle table and warp prefix-sum emit of one cell per lane;
 // every lane of the warp calls it (valid == false for lanes without a cell).
+// The warp's triangles take one contiguous range of the output: each lane
+// puts its vertex positions at its offset in the warp's staging buffer, and
+// the warp then writes the range with consecutive lanes on consecutive
+// floats (coalesced stores).
 __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const gh_mesh &out, bool valid, int i, int j,
-                                           int k, const float (&fv)[8]) {
+                                           int k, const float (&fv)[8], float *stage) {
     const int N = g.N, N1 = N + 1;
     const unsigned long long N13 = (unsigned long long)N1 * N1 * N1;
     const int lane = threadIdx.x & 31;
@@ -609,12 +627,12 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
         if (lane >= o) x += y;
     }
     const int wtot = __shfl_sync(FULL, x, 31);
-    unsigned long long tbase = 0;
+    unsigned long long wbase = 0;
     if (wtot) {
-        if (lane == 31) tbase = atomicAdd(&ctr->tris, (unsigned long long)wtot);
-        tbase = __shfl_sync(FULL, tbase, 31);
+        if (lane == 31) wbase = atomicAdd(&ctr->tris, (unsigned long long)wtot);
+        wbase = __shfl_sync(FULL, wbase, 31);
     }
-    tbase += (unsigned long long)(x - nt);
+    const int loc = x - nt;  // this lane's first triangle within the warp's range
     const unsigned sm = __ballot_sync(FULL, surf);
     if (sm && out.cell_ids) {
         unsigned long long cbase = 0;
@@ -630,10 +648,9 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
     } else if (sm && lane == 0) {
         atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
     }
+    if (!wtot) return;
     for (int t = 0; t < nt; ++t) {
-        const unsigned long long ti = tbase + t;
-        if (ti >= (unsigned long long)out.capacity_tris) break;
-        float pos[9];
+        float *pos = stage + 9 * (loc + t);
         unsigned long long key[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -656,22 +673,28 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
             key[v] = (unsigned long long)ax * N13 + (unsigned long long)la +
                      (unsigned long long)N1 * ((unsigned long long)lb + (unsigned long long)N1 * lc);
         }
-        float *dst = out.tri_xyz + ti * 9;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dst[q] = pos[q];
-        if (out.tri_keys) {
+        const unsigned long long ti = wbase + (unsigned long long)(loc + t);
+        if (out.tri_keys && ti < (unsigned long long)out.capacity_tris) {
             unsigned long long *kd = reinterpret_cast<unsigned long long *>(out.tri_keys) + ti * 3;
             kd[0] = key[0];
             kd[1] = key[1];
             kd[2] = key[2];
         }
     }
+    __syncwarp();
+    // the warp's range [wbase, wbase + wtot) of triangles, float by float
+    const unsigned long long cap = (unsigned long long)out.capacity_tris;
+    const unsigned long long nf = wbase >= cap ? 0ull : 9ull * ((wbase + wtot > cap ? cap : wbase + wtot) - wbase);
+    float *dst = out.tri_xyz + 9 * wbase;
+    for (unsigned long long f = lane; f < nf; f += 32) dst[f] = stage[f];
+    __syncwarp();  // the buffer is free for the warp's next cells
 }
 
 __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
+    __shared__ float stage[8][EMIT_STAGE];
     if (s.ctr->flags & STOP_FLAGS) return;
     const unsigned long long M = s.ctr->marks;
-    const int N = g.N, N1 = N + 1;
+    const int N = g.N;
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long m0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); m0 < M;
@@ -686,15 +709,15 @@ __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
             k = (int)mark_k(r);
             i = (int)(col / (uint32_t)N);
             j = (int)(col - (uint32_t)i * N);
+            const uint4 ci = *reinterpret_cast<const uint4 *>(s.cidx + 4 * m);
+            const uint32_t vi[4] = {ci.x, ci.y, ci.z, ci.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
-                const uint32_t idx = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], (uint32_t)k);
-                fv[q] = s.vval[idx];
-                fv[q + 4] = s.vval[idx + 1];
+                fv[q] = s.vval[vi[q]];
+                fv[q + 4] = s.vval[vi[q] + 1];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
     }
 }
 
@@ -721,6 +744,7 @@ void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s
 }
 
 __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh out) {
+    __shared__ float stage[8][EMIT_STAGE];
     const long long N = g.N, N1 = N + 1, n = N * N * N;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -739,7 +763,7 @@ __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh ou
                 fv[b] = s.lat[a + N1 * (bb + N1 * c)];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
     }
 }
 
@@ -758,6 +782,184 @@ void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cu
 
 void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st) {
     k_mc<<<nsm * 8, 256, 0, st>>>(g, s, out);
+}
+
+// ---------------------------------------------------------------------------
+// Continuation (Sec. 2), analytic SDBs: from seed cells the surface is crawled
+// cell by cell -- a cell's surface leaves it through exactly the faces whose
+// four corners do not all have one sign, so the neighbour across each such
+// face is a surface cell and is queued once (visited bit per cell).  Each
+// queued cell gets Marching Cubes at once from its own eight corner values
+// (the hopper's evaluator at the same lattice points, so the triangles are
+// bit-identical to the other methods').  Persistent warps take up to 32
+// queued cells at a time; the queue (in the marks buffer, cell id + 1 per
+// slot, 0 = not yet written) ends when no cell is queued and none is being
+// processed (q_pending == 0).  Waits are bounded (2 s of %globaltimer).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long CONT_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Marks cell c visited; true when this call did (the caller queues it).
+__device__ __forceinline__ bool visit(uint32_t *vis, unsigned long long c) {
+    const uint32_t bit = 1u << (uint32_t)(c & 31ull);
+    return (atomicOr(vis + (c >> 5), bit) & bit) == 0u;
+}
+
+// Queues cell c: false when the queue is full (the overflow flag is set and
+// the cell is dropped; the caller does not count it as pending).
+__device__ __forceinline__ bool enqueue(const Scratch &s, unsigned long long c) {
+    const unsigned long long slot = atomicAdd(&s.ctr->marks, 1ull);
+    if (slot >= (unsigned long long)s.cap_marks) {
+        atomicOr(&s.ctr->flags, FLAG_MARK_OVERFLOW);
+        return false;
+    }
+    *reinterpret_cast<volatile unsigned long long *>(s.marks_raw + slot) = c + 1ull;
+    return true;
+}
+
+// One thread per seed point: the cell holding it, then the first sign change
+// along the lattice line (a, j0, k0), a = i0 .. N, in +x order.
+__global__ void k_cont_seed(const Prim *__restrict__ gprims, int nprim, GridP g, Scratch s,
+                            const float *__restrict__ seeds, int n_seeds) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_seeds) return;
+    const int N = g.N;
+    int ijk[3];
+    for (int a = 0; a < 3; ++a) {
+        const float x = floorf((seeds[3 * t + a] - g.lo[a]) * g.inv_h);
+        ijk[a] = x < 0.f ? 0 : (x > (float)(N - 1) ? N - 1 : (int)x);
+    }
+    const float y = fmaf((float)ijk[1], g.h, g.lo[1]), z = fmaf((float)ijk[2], g.h, g.lo[2]);
+    float fp = csg_eval(sprim, nprim, fmaf((float)ijk[0], g.h, g.lo[0]), y, z);
+    unsigned long long evals = 1;
+    for (int a = ijk[0]; a < N; ++a) {
+        const float fn = csg_eval(sprim, nprim, fmaf((float)(a + 1), g.h, g.lo[0]), y, z);
+        ++evals;
+        if ((fp < 0.f) != (fn < 0.f)) {
+            const unsigned long long c = ((unsigned long long)a * N + ijk[1]) * N + ijk[2];
+            if (visit(s.vis, c) && enqueue(s, c)) atomicAdd(&s.ctr->q_pending, 1ull);
+            break;
+        }
+        fp = fn;
+    }
+    atomicAdd(&s.ctr->hop_evals, evals);
+}
+
+__global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprims, int nprim, GridP g, Scratch s,
+                                                  gh_mesh out) {
+    extern __shared__ float4 sprim[];
+    __shared__ float stage[8][EMIT_STAGE];
+    load_prims(sprim, gprims, nprim);
+    const int N = g.N;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long cap = (unsigned long long)s.cap_marks;
+    volatile unsigned long long *vq = reinterpret_cast<volatile unsigned long long *>(s.marks_raw);
+    volatile Counters *vc = s.ctr;
+    unsigned long long evals = 0;
+    for (;;) {
+        // claim up to 32 queued cells (lane 0), or learn that the crawl is over
+        unsigned long long h = 0;
+        int n = 0;
+        if (lane == 0) {
+            const unsigned long long t0 = gtimer_ns();
+            for (unsigned it = 1;; ++it) {
+                h = vc->q_head;
+                unsigned long long t = vc->marks;
+                t = t < cap ? t : cap;
+                if (h < t) {
+                    const int want = (int)(t - h < 32ull ? t - h : 32ull);
+                    if (atomicCAS(&s.ctr->q_head, h, h + (unsigned long long)want) == h) {
+                        n = want;
+                        break;
+                    }
+                    continue;
+                }
+                if (vc->q_pending == 0ull || (vc->flags & FLAG_TIMEOUT)) break;
+                if ((it & 63u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
+                    atomicOr(&s.ctr->flags, FLAG_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        n = __shfl_sync(FULL, n, 0);
+        h = __shfl_sync(FULL, h, 0);
+        if (n == 0) break;
+        const bool valid = lane < n;
+        unsigned long long c = 0;
+        if (valid) {
+            // the pusher writes the slot right after reserving it
+            const unsigned long long t0 = gtimer_ns();
+            unsigned long long v;
+            for (unsigned it = 1;; ++it) {
+                v = vq[h + lane];
+                if (v) break;
+                if ((it & 63u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
+                    atomicOr(&s.ctr->flags, FLAG_TIMEOUT);
+                    break;
+                }
+            }
+            c = v ? v - 1ull : 0ull;
+        }
+        const int k = (int)(c % (unsigned long long)N), j = (int)((c / N) % N), i = (int)(c / ((unsigned long long)N * N));
+        float fv[8];
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const float f = csg_eval(sprim, nprim, fmaf((float)(i + (b & 1)), g.h, g.lo[0]),
+                                         fmaf((float)(j + ((b >> 1) & 1)), g.h, g.lo[1]),
+                                         fmaf((float)(k + (b >> 2)), g.h, g.lo[2]));
+                if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                fv[b] = f;
+            }
+            evals += 8;
+        }
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
+        // the neighbours across the faces the surface crosses
+        long long pushed = 0;
+        if (valid) {
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    int neg = 0;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b)
+                        if (((b >> ax) & 1) == side) neg += fv[b] < 0.f;
+                    if (neg == 0 || neg == 4) continue;
+                    int n3[3] = {i, j, k};
+                    n3[ax] += side ? 1 : -1;
+                    if (n3[ax] < 0 || n3[ax] >= N) continue;
+                    const unsigned long long nc = ((unsigned long long)n3[0] * N + n3[1]) * N + n3[2];
+                    if (visit(s.vis, nc) && enqueue(s, nc)) ++pushed;
+                }
+            pushed -= 1;  // this cell is finished
+        }
+        __threadfence();  // the queued slots are visible before the count says so
+        for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(FULL, pushed, o);
+        if (lane == 0 && pushed) atomicAdd(&s.ctr->q_pending, (unsigned long long)pushed);
+    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
+    if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
+}
+
+void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, const float *seeds, int n_seeds,
+                     const gh_mesh &out, int nsm, cudaStream_t st) {
+    const size_t smem = (size_t)nprim * sizeof(Prim);
+    const unsigned long long ncell = (unsigned long long)g.N * g.N * g.N;
+    cudaMemsetAsync(s.vis, 0, sizeof(uint32_t) * ((ncell + 31) / 32), st);
+    k_cont_seed<<<(n_seeds + 127) / 128, 128, smem, st>>>(prims, nprim, g, s, seeds, n_seeds);
+    cudaFuncSetAttribute(k_cont_csg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cont_csg, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_cont_csg<<<nsm * per_sm, 256, smem, st>>>(prims, nprim, g, s, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -780,7 +982,6 @@ __global__ void k_refine_zero(Scratch s) {
 __global__ void k_refine_select(GridP g, Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
     const unsigned long long M = s.ctr->marks;
-    const int N = g.N, N1 = N + 1;
     // the 12 cube edges as corner pairs (corner b at (b&1, b>>1&1, b>>2&1))
     const uint8_t ea[12] = {0, 2, 4, 6, 0, 1, 4, 5, 0, 1, 2, 3};
     const uint8_t eb[12] = {1, 3, 5, 7, 2, 3, 6, 7, 4, 5, 6, 7};
@@ -788,18 +989,18 @@ __global__ void k_refine_select(GridP g, Scratch s) {
          m += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long r = s.marks_csr[m];
         if (mark_empty(r)) continue;  // no corners evaluated, no crossing edge
-        const uint32_t col = mark_col(r), k = mark_k(r);
-        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
         uint32_t vi[8];
         float fv[8];
+        const uint4 ci = *reinterpret_cast<const uint4 *>(s.cidx + 4 * m);
+        vi[0] = ci.x;
+        vi[1] = ci.y;
+        vi[2] = ci.z;
+        vi[3] = ci.w;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
-            const uint32_t idx = find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], k);
-            vi[q] = idx;
-            vi[q + 4] = idx + 1;
-            fv[q] = s.vval[idx];
-            fv[q + 4] = s.vval[idx + 1];
+            vi[q + 4] = vi[q] + 1;
+            fv[q] = s.vval[vi[q]];
+            fv[q + 4] = s.vval[vi[q] + 1];
         }
         uint32_t need = 0;
 #pragma unroll

@@ -109,6 +109,8 @@ def lib():
                 "gh_last_profile": (ctypes.c_int, [ctypes.POINTER(Profile)]),
                 "gh_release_cache": (ctypes.c_int, []),
                 "gh_column_order": (I64, [I32, I64]),
+                "gh_polygonize_cont": (ctypes.c_int, [ctypes.POINTER(Grid), P, P, I32, ctypes.POINTER(Options),
+                                                      ctypes.POINTER(MeshDesc), P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -123,7 +125,7 @@ def exported_symbols():
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
             "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc", "gh_batch_graph_launch",
-            "gh_batch_graph_free", "gh_release_cache", "gh_column_order"]
+            "gh_batch_graph_free", "gh_release_cache", "gh_column_order", "gh_polygonize_cont"]
 
 
 def check(rc):
@@ -356,6 +358,35 @@ def polygonize(sdb: Sdb, N, lo=-1.0, hi=1.0, precision="fp32", tau_mode=GH_TAU_D
                         bufs.stats_dict(), bufs.verts[:V] if indexed else None,
                         bufs.faces[:T] if indexed else None)
         cap = int(max(counts[0], counts[1], 2 * counts[2]) * 1.1) + 4096
+    raise GhError(GH_ERR_CAPACITY, "output buffers kept overflowing")
+
+
+def polygonize_cont_into(sdb: Sdb, N, seeds, bufs: Buffers, lo=-1.0, hi=1.0, sync=True, stream=None) -> int:
+    """gh_polygonize_cont (continuation from seed points, analytic SDBs) into
+    preallocated buffers; returns the status (GH_ERR_CAPACITY returned)."""
+    sp = np.ascontiguousarray(seeds, np.float32).reshape(-1, 3)
+    g = _grid(N, lo, hi)
+    o = options("fp32", GH_TAU_DIAGONAL, None, sync)
+    rc = lib().gh_polygonize_cont(ctypes.byref(g), sdb.handle, sp.ctypes.data, sp.shape[0], ctypes.byref(o),
+                                  ctypes.byref(bufs.desc), _stream_ptr(stream))
+    if rc not in (GH_OK, GH_ERR_CAPACITY):
+        check(rc)
+    return rc
+
+
+def polygonize_cont(sdb: Sdb, N, seeds, lo=-1.0, hi=1.0, keys=False, cells=False, stream=None) -> Mesh:
+    """Continuation with buffers sized automatically (see polygonize)."""
+    cap = 4 * int(N) * int(N) + 4096
+    for _ in range(3):
+        bufs = Buffers(cap, keys=keys, cap_cells=cap if cells else 0)
+        rc = polygonize_cont_into(sdb, N, seeds, bufs, lo, hi, True, stream)
+        counts = bufs.counts.cpu().numpy()
+        if rc == GH_OK:
+            T, C = int(counts[0]), int(counts[1])
+            return Mesh(bufs.tri_xyz[:T], bufs.tri_keys[:T] if keys else None,
+                        bufs.cell_ids[:C] if cells else None, bufs.cell_cases[:C] if cells else None,
+                        bufs.stats_dict())
+        cap = int(max(counts[0], counts[1]) * 1.1) + 4096
     raise GhError(GH_ERR_CAPACITY, "output buffers kept overflowing")
 
 
