@@ -376,7 +376,7 @@ extern "C" int gh_release_cache(void) {
         cudaSetDevice(e.device);
         Scratch &c = e.scr;
         void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                        c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.cidx, c.vis};
+                        c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.vis};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -414,7 +414,7 @@ extern "C" int gh_create_sdb(const gh_sdb_desc *desc, gh_sdb **out) {
 static void free_scratch(gh_sdb *s) {
     Scratch &c = s->scr;
     void *ptrs[] = {c.ctr, c.marks_raw, c.marks_csr, c.colcount, c.coloff, c.linecount, c.lineoff,
-                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.cidx, c.vis};
+                    c.blocksum, c.vkey, c.vval, c.vflag, c.rlist, c.lat, c.ebase, c.ebsum, c.vis};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->scr = Scratch{};
@@ -478,7 +478,6 @@ static int ensure_scratch(gh_sdb *s, int N, long long want_marks, long long want
     GH_CUDA(cudaMalloc((void **)&c.ctr, sizeof(Counters)));
     GH_CUDA(cudaMalloc((void **)&c.marks_raw, sizeof(unsigned long long) * cm));
     GH_CUDA(cudaMalloc((void **)&c.marks_csr, sizeof(unsigned long long) * cm));
-    GH_CUDA(cudaMalloc((void **)&c.cidx, sizeof(uint32_t) * 4 * cm));
     GH_CUDA(cudaMalloc((void **)&c.colcount, sizeof(uint32_t) * ncols));
     GH_CUDA(cudaMalloc((void **)&c.coloff, sizeof(uint32_t) * (ncols + 1)));
     GH_CUDA(cudaMalloc((void **)&c.linecount, sizeof(uint32_t) * nlines));
@@ -949,11 +948,30 @@ struct BatchPlan {
 static std::mutex g_graph_mu;
 static std::vector<std::pair<void *, Item *>> g_graph_items;
 
+// The launch sequence of a batch: a fixed number of launches whatever B is --
+// counter reset, one persistent hopping launch per evaluator family, the
+// line lists, the vertex values (one launch for the analytic items, one per
+// neural family), the refinement selection and refinement, Marching Cubes
+// and the status words, each step one launch over all items (the indexed
+// mesh, when asked for, adds two launches per item that wants it).
 static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_options &o, const gh_mesh *outs,
                          int nsm, cudaStream_t st) {
     const int tiles = o.mlp_tiles == 1 ? 1 : 2;
-    for (int b = 0; b < B; ++b) launch_init(sd[b]->scr, st);
+    int max_N = 2, max_prims = 1;
+    bool any_csg = false, any_mlp = false;
+    for (int b = 0; b < B; ++b) {
+        max_N = P.g[b].N > max_N ? P.g[b].N : max_N;
+        if (sd[b]->kind == GH_SDB_CSG) {
+            any_csg = true;
+            max_prims = sd[b]->nprim > max_prims ? sd[b]->nprim : max_prims;
+        } else {
+            any_mlp = true;
+        }
+    }
+    long long launches = 1 + 8 + 1 + 1;  // counters, lists, Marching Cubes, status words
+    launch_init_b(P.d_items, B, st);
     for (auto &gr : P.groups) {
+        ++launches;
         const gh_sdb *first = sd[P.order[gr.first]];
         const Item *di = P.d_items + gr.first;
         const int n = gr.second - gr.first;
@@ -967,33 +985,42 @@ static int batch_enqueue(const BatchPlan &P, int B, gh_sdb *const *sd, const gh_
             launch_hop_mlp_bf16(di, n, first->mlp.width, nsm, tiles, st);
         }
     }
-    for (int b = 0; b < B; ++b) launch_build_lists(P.g[b], sd[b]->scr, st);
+    launch_build_lists_b(P.d_items, B, max_N, nsm, st);
+    if (any_csg) {
+        launch_eval_vertices_csg_b(P.d_items, B, max_prims, nsm, st);
+        ++launches;
+    }
     for (auto &gr : P.groups) {
         const gh_sdb *first = sd[P.order[gr.first]];
+        if (first->kind == GH_SDB_CSG) continue;
         const Item *di = P.d_items + gr.first;
         const int n = gr.second - gr.first;
-        if (first->kind == GH_SDB_CSG) {
-            for (int q = gr.first; q < gr.second; ++q) {
-                const int b = P.order[q];
-                launch_eval_vertices_csg(sd[b]->d_prims, sd[b]->nprim, P.g[b], sd[b]->scr, nsm, st);
-            }
-        } else if (o.precision == GH_FP32) {
-            launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, false, st);
-        } else {
-            launch_eval_vertices_mlp_bf16(di, n, first->mlp.width, nsm, tiles, st);
-            for (int q = gr.first; q < gr.second; ++q) {
-                const int b = P.order[q];
-                launch_refine_select(P.g[b], sd[b]->scr, st);
-            }
+        ++launches;
+        if (o.precision == GH_FP32) launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, false, st);
+        else launch_eval_vertices_mlp_bf16(di, n, first->mlp.width, nsm, tiles, st);
+    }
+    if (any_mlp && o.precision != GH_FP32) {
+        launch_refine_select_b(P.d_items, B, nsm, st);
+        launches += 3;
+        for (auto &gr : P.groups) {
+            const gh_sdb *first = sd[P.order[gr.first]];
+            if (first->kind == GH_SDB_CSG) continue;
+            const Item *di = P.d_items + gr.first;
+            const int n = gr.second - gr.first;
+            ++launches;
             if (o.precision == GH_BF16_REFINE_X6) launch_refine_mlp_x6(di, n, first->mlp.width, nsm, st);
             else launch_eval_vertices_mlp_fp32(di, n, first->mlp.width, nsm, true, st);
         }
     }
-    for (int b = 0; b < B; ++b) {
-        launch_mc(P.g[b], sd[b]->scr, outs[b], nsm, st);
-        if (wants_index(outs[b])) launch_index_mesh(P.g[b], sd[b]->scr, outs[b], nsm, st);
-        launch_finalize(sd[b]->scr, outs[b], (long long)P.g[b].N * P.g[b].N, st);
-    }
+    launch_mc_b(P.d_items, B, nsm, st);
+    for (int b = 0; b < B; ++b)
+        if (wants_index(outs[b])) {
+            launch_index_mesh(P.g[b], sd[b]->scr, outs[b], nsm, st);
+            launches += 5;  // at most
+        }
+    launch_finalize_b(P.d_items, B, st);
+    g_prof.recorded = false;
+    g_prof.launches = launches;
     GH_CUDA(cudaGetLastError());
     return GH_OK;
 }
@@ -1067,7 +1094,10 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
                 cudaFree(d_items);
                 return rc;
             }
-        for (int q = 0; q < B; ++q) h_items[q] = make_item(sd[P.order[q]], P.g[P.order[q]]);
+        for (int q = 0; q < B; ++q) {
+            h_items[q] = make_item(sd[P.order[q]], P.g[P.order[q]]);
+            h_items[q].out = outs[P.order[q]];
+        }
         GH_CUDA(cudaMemcpyAsync(d_items, h_items.data(), sizeof(Item) * B, cudaMemcpyHostToDevice, st));
         if ((rc = batch_enqueue(P, B, sd.data(), o, outs, nsm, st))) {
             cudaFree(d_items);
@@ -1305,15 +1335,12 @@ extern "C" int gh_polygonize_csg_noalloc(const gh_grid *grid, const gh_csg_prim 
     off += up256(4 * (nlines + 1));
     c.blocksum = (uint32_t *)(q + off);
     off += up256(4 * 4096);
-    // marks raw + grouped + their corner indices, two vertices (key + value) per mark
-    const size_t per = 2 * 8 + 16 + 2 * (8 + 4);
+    const size_t per = 2 * 8 + 2 * (8 + 4);  // marks raw + grouped, two vertices (key + value) per mark
     const size_t M = ((GH_NOALLOC_SCRATCH_BYTES - off - 4 * 256) / per) & ~(size_t)255;
     c.marks_raw = (unsigned long long *)(q + off);
     off += up256(8 * M);
     c.marks_csr = (unsigned long long *)(q + off);
     off += up256(8 * M);
-    c.cidx = (uint32_t *)(q + off);
-    off += up256(16 * M);
     c.vkey = (unsigned long long *)(q + off);
     off += up256(8 * 2 * M);
     c.vval = (float *)(q + off);

@@ -160,8 +160,6 @@ struct Scratch {
     uint32_t *lineoff;              // [(N+1)^2 + 1]
     uint32_t *blocksum;             // scan partials
     unsigned long long *vkey;       // line | c << 32, grouped by line, c ascending
-    uint32_t *cidx;                 // [cap_marks][4]: vertex-list index of corner (q, c = k) of each
-                                    // grouped mark not proven empty, q = ox + 2 oy
     float *vval;                    // [cap_verts]
     uint8_t *vflag;                 // [cap_verts] refinement flags
     uint32_t *rlist;                // [cap_verts] vertices to refine
@@ -184,6 +182,7 @@ struct Item {
     const Prim *prims;  // analytic SDB (kind 0)
     int nprim;
     int kind;
+    gh_mesh out;        // batches: the item's output buffers (single calls pass them as a launch argument)
 };
 
 // Packing of mark records.  MARK_EMPTY: the hop value proves that the cell
@@ -220,6 +219,14 @@ void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s
 void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st);
 void launch_enum_stats(const GridP &g, Scratch &s, cudaStream_t st);
 void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st);
+// batches: each per-item step of the pipeline as one launch over all n items
+// (every CTA walks the items in order and takes its share of each)
+void launch_init_b(const Item *items, int n, cudaStream_t st);
+void launch_build_lists_b(const Item *items, int n, int max_N, int nsm, cudaStream_t st);
+void launch_eval_vertices_csg_b(const Item *items, int n, int max_prims, int nsm, cudaStream_t st);
+void launch_refine_select_b(const Item *items, int n, int nsm, cudaStream_t st);  // neural items only
+void launch_mc_b(const Item *items, int n, int nsm, cudaStream_t st);
+void launch_finalize_b(const Item *items, int n, cudaStream_t st);
 // continuation (Sec. 2) for analytic SDBs: seed search from host-given points
 // (seeds: device [n][3]) and the surface crawl with Marching Cubes per cell
 void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, const float *seeds, int n_seeds,

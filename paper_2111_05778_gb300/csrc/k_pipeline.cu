@@ -23,7 +23,7 @@
 namespace gh {
 
 __constant__ uint8_t c_tab_n[256];
-__constant__ uint8_t c_tab_e[256][16];
+__constant__ __align__(16) uint8_t c_tab_e[256][16];
 
 cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges) {
     uint8_t n[256], e[256][16];
@@ -360,17 +360,55 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, 
     return r;
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
-                                                         uint32_t *__restrict__ bsum, const Counters *ctr) {
-    __shared__ uint32_t wsum[32];
-    if (ctr->flags & STOP_FLAGS) return;
-    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+// One tile of the reduction pass (whole block): bsum[tile] = its sum.
+__device__ __forceinline__ void scan_reduce_tile(const uint32_t *__restrict__ in, long long n,
+                                                 uint32_t *__restrict__ bsum, long long tile, uint32_t *wsum) {
+    const long long base = tile * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
     uint32_t v = 0;
     for (int i = 0; i < SCAN_IPT; ++i)
         if (base + i < n) v += in[base + i];
     uint32_t tot;
     block_excl_scan(v, wsum, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    if (threadIdx.x == 0) bsum[tile] = tot;
+}
+
+// One tile of the apply pass (whole block); the last tile writes out[n] and *total.
+__device__ __forceinline__ void scan_apply_tile(const uint32_t *__restrict__ in, long long n,
+                                                const uint32_t *__restrict__ bsum, uint32_t *__restrict__ out,
+                                                unsigned long long *total, long long tile, long long ntiles,
+                                                uint32_t *wsum, uint32_t *prefix) {
+    // prefix of this tile = sum of the partials before it
+    uint32_t p = 0;
+    for (long long i = threadIdx.x; i < tile; i += blockDim.x) p += bsum[i];
+    uint32_t ptot;
+    block_excl_scan(p, wsum, ptot);
+    if (threadIdx.x == 0) *prefix = ptot;
+    __syncthreads();
+    const uint32_t pre = *prefix;
+    const long long base = tile * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
+    uint32_t v[SCAN_IPT], sum = 0;
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = pre + block_excl_scan(sum, wsum, tot);
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) {
+        out[n] = pre + tot;
+        if (total) *total = (unsigned long long)(pre + tot);
+    }
+    __syncthreads();  // *prefix is rewritten by the block's next tile
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
+                                                         uint32_t *__restrict__ bsum, const Counters *ctr) {
+    __shared__ uint32_t wsum[32];
+    if (ctr->flags & STOP_FLAGS) return;
+    scan_reduce_tile(in, n, bsum, blockIdx.x, wsum);
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const uint32_t *__restrict__ in, long long n,
@@ -379,29 +417,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const uint32_t *__restric
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t prefix;
     if (ctr->flags & STOP_FLAGS) return;
-    // prefix of this block = sum of the partials before it
-    uint32_t p = 0;
-    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) p += bsum[i];
-    uint32_t ptot;
-    block_excl_scan(p, wsum, ptot);
-    if (threadIdx.x == 0) prefix = ptot;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_IPT;
-    uint32_t v[SCAN_IPT], sum = 0;
-    for (int i = 0; i < SCAN_IPT; ++i) {
-        v[i] = base + i < n ? in[base + i] : 0u;
-        sum += v[i];
-    }
-    uint32_t tot;
-    uint32_t run = prefix + block_excl_scan(sum, wsum, tot);
-    for (int i = 0; i < SCAN_IPT; ++i) {
-        if (base + i < n) out[base + i] = run;
-        run += v[i];
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        out[n] = prefix + tot;
-        if (total) *total = (unsigned long long)(prefix + tot);
-    }
+    scan_apply_tile(in, n, bsum, out, total, blockIdx.x, gridDim.x, wsum, &prefix);
 }
 
 static void scan_u32(const uint32_t *in, long long n, uint32_t *out, uint32_t *bsum, unsigned long long *total,
@@ -421,15 +437,18 @@ long long scan_partials(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 
 // ---------------------------------------------------------------------------
 // Marks grouped by column.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter_marks(Scratch s) {
-    if (s.ctr->flags & STOP_FLAGS) return;
+__device__ __forceinline__ void scatter_marks(const Scratch &s, unsigned long long t0, unsigned long long stride) {
     const unsigned long long M = s.ctr->marks;
-    for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
-         m += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long m = t0; m < M; m += stride) {
         const unsigned long long r = s.marks_raw[m];
         const uint32_t col = mark_col(r);
         s.marks_csr[s.coloff[col] + mark_rank(r)] = r & (0xFFFFFFFFFFull | MARK_EMPTY);
     }
+}
+
+__global__ void k_scatter_marks(Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    scatter_marks(s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x, (unsigned long long)gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -454,17 +473,15 @@ __device__ __forceinline__ void set_cells(uint32_t *bits, unsigned long long r) 
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
-    extern __shared__ uint32_t lbits[];
-    if (s.ctr->flags & STOP_FLAGS) return;
+__device__ __forceinline__ void lines_pass(const GridP &g, const Scratch &s, long long t0, long long stride,
+                                           uint32_t *lbits) {
     const int N = g.N, N1 = N + 1, NW = (N1 + 31) >> 5;
     uint32_t *bits = lbits + threadIdx.x;  // word w at bits[w * LINES_T]
     const unsigned long long *__restrict__ mk = s.marks_csr;
     const uint32_t *__restrict__ off = s.coloff;
     const long long nlines = (long long)N1 * N1;
     const unsigned long long cap = (unsigned long long)s.cap_verts;
-    for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
-         line += (long long)gridDim.x * blockDim.x) {
+    for (long long line = t0; line < nlines; line += stride) {
         const int a = (int)(line / N1), b = (int)(line - (long long)a * N1);
         for (int w = 0; w < NW; ++w) bits[w * LINES_T] = 0u;
         for (int di = -1; di <= 0; ++di)
@@ -489,8 +506,7 @@ __global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
             for (int w = 0; w < NW; ++w) cnt += (uint32_t)__popc(bits[w * LINES_T]);
             s.linecount[line] = cnt;
         } else {
-            const uint32_t lbase = s.lineoff[line];
-            unsigned long long o = lbase;
+            unsigned long long o = s.lineoff[line];
             for (int w = 0; w < NW; ++w) {
                 uint32_t v = bits[w * LINES_T];
                 while (v) {
@@ -500,27 +516,15 @@ __global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
                     ++o;
                 }
             }
-            // the list index of vertex (line, k) for every mark of the four
-            // columns around the line: the rank of bit k in the line's set (the
-            // marks of a column come in ascending k, so one pass over the words)
-            for (int di = -1; di <= 0; ++di)
-                for (int dj = -1; dj <= 0; ++dj) {
-                    const int i = a + di, j = b + dj;
-                    if (i < 0 || j < 0 || i >= N || j >= N) continue;
-                    const uint32_t q = (uint32_t)(-di) + 2u * (uint32_t)(-dj);
-                    const uint32_t col = (uint32_t)i * N + j;
-                    int w = 0;
-                    uint32_t below = 0;
-                    for (uint32_t m = off[col], e = off[col + 1]; m < e; ++m) {
-                        const unsigned long long r = __ldg(mk + m);
-                        if (mark_empty(r)) continue;
-                        const uint32_t k = mark_k(r);
-                        for (; w < (int)(k >> 5); ++w) below += (uint32_t)__popc(bits[w * LINES_T]);
-                        s.cidx[4ull * m + q] = lbase + below + (uint32_t)__popc(bits[w * LINES_T] & ((1u << (k & 31)) - 1u));
-                    }
-                }
         }
     }
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(LINES_T) k_lines(GridP g, Scratch s) {
+    extern __shared__ uint32_t lbits[];
+    if (s.ctr->flags & STOP_FLAGS) return;
+    lines_pass<EMIT>(g, s, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, lbits);
 }
 
 __global__ void k_check_verts(Scratch s) {
@@ -551,20 +555,25 @@ __device__ __forceinline__ void vertex_pos(const GridP &g, unsigned long long ke
     z = fmaf((float)c, g.h, g.lo[2]);
 }
 
-__global__ void __launch_bounds__(256) k_eval_vertices_csg(const Prim *__restrict__ gprims, int nprim, GridP g,
-                                                            Scratch s) {
-    extern __shared__ float4 sprim[];
-    load_prims(sprim, gprims, nprim);
-    if (s.ctr->flags & STOP_FLAGS) return;
+__device__ __forceinline__ void eval_vertices_csg(const float4 *sprim, int nprim, const GridP &g, const Scratch &s,
+                                                  unsigned long long t0, unsigned long long stride) {
     const unsigned long long V = s.ctr->verts;
-    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
-         v += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long v = t0; v < V; v += stride) {
         float x, y, z;
         vertex_pos(g, s.vkey[v], x, y, z);
         const float f = csg_eval(sprim, nprim, x, y, z);
         if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
         s.vval[v] = f;
     }
+}
+
+__global__ void __launch_bounds__(256) k_eval_vertices_csg(const Prim *__restrict__ gprims, int nprim, GridP g,
+                                                            Scratch s) {
+    extern __shared__ float4 sprim[];
+    load_prims(sprim, gprims, nprim);
+    if (s.ctr->flags & STOP_FLAGS) return;
+    eval_vertices_csg(sprim, nprim, g, s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x,
+                      (unsigned long long)gridDim.x * blockDim.x);
 }
 
 void launch_eval_vertices_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, int nsm,
@@ -597,6 +606,38 @@ void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long l
 // ---------------------------------------------------------------------------
 // 5. Marching Cubes on the marked cells.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t find_c(const unsigned long long *__restrict__ vkey, uint32_t lo, uint32_t hi,
+                                           uint32_t c) {
+    // vkey[lo..hi) has ascending c (upper 32 bits); c is present by construction
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)(vkey[mid] >> 32) <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// list index of corner (q, c = k) of marked cell (i, j, k), q = ox + 2 oy
+__device__ __forceinline__ uint32_t corner_index(const Scratch &s, int N1, int i, int j, int k, int q) {
+    const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
+    return find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], (uint32_t)k);
+}
+
+// The Marching Cubes table in shared memory: the lanes of a warp look up
+// different cases, which the constant bank would serve one address at a time.
+struct __align__(16) McTab {
+    uint8_t e[256][16];
+    uint8_t n[256];
+};
+
+// Whole block; ends with __syncthreads.
+__device__ __forceinline__ void load_tab(McTab &t) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        *reinterpret_cast<uint4 *>(t.e[i]) = *reinterpret_cast<const uint4 *>(c_tab_e[i]);
+        t.n[i] = c_tab_n[i];
+    }
+    __syncthreads();
+}
+
 // Triangles a warp stages in shared memory before writing them out: at most
 // 5 per cell, 32 cells, 9 floats each.
 constexpr int EMIT_STAGE = 32 * 5 * 9;
@@ -608,7 +649,7 @@ constexpr int EMIT_STAGE = 32 * 5 * 9;
 // the warp then writes the range with consecutive lanes on consecutive
 // floats (coalesced stores).
 __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const gh_mesh &out, bool valid, int i, int j,
-                                           int k, const float (&fv)[8], float *stage) {
+                                           int k, const float (&fv)[8], float *stage, const McTab &tab) {
     const int N = g.N, N1 = N + 1;
     const unsigned long long N13 = (unsigned long long)N1 * N1 * N1;
     const int lane = threadIdx.x & 31;
@@ -619,7 +660,7 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
         for (int b = 0; b < 8; ++b) cs |= (fv[b] < 0.f) << b;
     }
     const bool surf = valid && cs != 0 && cs != 255;
-    const int nt = surf ? c_tab_n[cs] : 0;
+    const int nt = surf ? tab.n[cs] : 0;
     // warp-exclusive prefix sum of the triangle counts, one atomic per warp
     int x = nt;
     for (int o = 1; o < 32; o <<= 1) {
@@ -654,7 +695,7 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
         unsigned long long key[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            const int e = c_tab_e[cs][3 * t + v];
+            const int e = tab.e[cs][3 * t + v];
             const int ax = e >> 2, u = e & 1, w = (e >> 1) & 1;
             const int ox = ax == 0 ? 0 : u, oy = ax == 1 ? 0 : (ax == 0 ? u : w), oz = ax == 2 ? 0 : w;
             const int blo = ox + 2 * oy + 4 * oz, bhi = blo + (1 << ax);
@@ -690,15 +731,14 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
     __syncwarp();  // the buffer is free for the warp's next cells
 }
 
-__global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
-    __shared__ float stage[8][EMIT_STAGE];
-    if (s.ctr->flags & STOP_FLAGS) return;
+// Marching Cubes on the marked cells; warps start at w0 (a multiple of 32)
+// and step by stride (a multiple of 32).
+__device__ __forceinline__ void mc_cells(const GridP &g, const Scratch &s, const gh_mesh &out, float *stage,
+                                         const McTab &tab, unsigned long long w0, unsigned long long stride) {
     const unsigned long long M = s.ctr->marks;
     const int N = g.N;
     const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long m0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); m0 < M;
-         m0 += stride) {
+    for (unsigned long long m0 = w0; m0 < M; m0 += stride) {
         const unsigned long long m = m0 + lane;
         const unsigned long long r = m < M ? s.marks_csr[m] : MARK_EMPTY;
         const bool valid = !mark_empty(r);  // cells marked empty have no triangles
@@ -709,16 +749,24 @@ __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
             k = (int)mark_k(r);
             i = (int)(col / (uint32_t)N);
             j = (int)(col - (uint32_t)i * N);
-            const uint4 ci = *reinterpret_cast<const uint4 *>(s.cidx + 4 * m);
-            const uint32_t vi[4] = {ci.x, ci.y, ci.z, ci.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                fv[q] = s.vval[vi[q]];
-                fv[q + 4] = s.vval[vi[q] + 1];
+                const uint32_t idx = corner_index(s, N + 1, i, j, k, q);
+                fv[q] = s.vval[idx];
+                fv[q + 4] = s.vval[idx + 1];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage, tab);
     }
+}
+
+__global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
+    __shared__ float stage[8][EMIT_STAGE];
+    __shared__ McTab tab;
+    if (s.ctr->flags & STOP_FLAGS) return;
+    load_tab(tab);
+    mc_cells(g, s, out, stage[threadIdx.x >> 5], tab, blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
+             (unsigned long long)gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -745,6 +793,8 @@ void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s
 
 __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh out) {
     __shared__ float stage[8][EMIT_STAGE];
+    __shared__ McTab tab;
+    load_tab(tab);
     const long long N = g.N, N1 = N + 1, n = N * N * N;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -763,7 +813,7 @@ __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh ou
                 fv[b] = s.lat[a + N1 * (bb + N1 * c)];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5], tab);
     }
 }
 
@@ -856,6 +906,8 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
                                                   gh_mesh out) {
     extern __shared__ float4 sprim[];
     __shared__ float stage[8][EMIT_STAGE];
+    __shared__ McTab tab;
+    load_tab(tab);
     load_prims(sprim, gprims, nprim);
     const int N = g.N;
     const int lane = threadIdx.x & 31;
@@ -920,7 +972,7 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
             }
             evals += 8;
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5]);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5], tab);
         // the neighbours across the faces the surface crosses
         long long pushed = 0;
         if (valid) {
@@ -971,33 +1023,32 @@ void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, c
 // endpoints of such edges are re-evaluated in FP32; every other corner keeps
 // its BF16 value, of which only the (certain) sign is ever used.
 // ---------------------------------------------------------------------------
-__global__ void k_refine_zero(Scratch s) {
-    if (s.ctr->flags & STOP_FLAGS) return;
+__device__ __forceinline__ void refine_zero(const Scratch &s, unsigned long long t0, unsigned long long stride) {
     const unsigned long long V = s.ctr->verts;
-    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
-         v += (unsigned long long)gridDim.x * blockDim.x)
-        s.vflag[v] = 0;
+    for (unsigned long long v = t0; v < V; v += stride) s.vflag[v] = 0;
 }
 
-__global__ void k_refine_select(GridP g, Scratch s) {
+__global__ void k_refine_zero(Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
+    refine_zero(s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x, (unsigned long long)gridDim.x * blockDim.x);
+}
+
+__device__ __forceinline__ void refine_select(const GridP &g, const Scratch &s, unsigned long long t0,
+                                              unsigned long long stride) {
     const unsigned long long M = s.ctr->marks;
     // the 12 cube edges as corner pairs (corner b at (b&1, b>>1&1, b>>2&1))
     const uint8_t ea[12] = {0, 2, 4, 6, 0, 1, 4, 5, 0, 1, 2, 3};
     const uint8_t eb[12] = {1, 3, 5, 7, 2, 3, 6, 7, 4, 5, 6, 7};
-    for (unsigned long long m = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; m < M;
-         m += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long m = t0; m < M; m += stride) {
         const unsigned long long r = s.marks_csr[m];
         if (mark_empty(r)) continue;  // no corners evaluated, no crossing edge
+        const uint32_t col = mark_col(r), k = mark_k(r);
+        const int i = (int)(col / (uint32_t)g.N), j = (int)(col - (uint32_t)i * g.N);
         uint32_t vi[8];
         float fv[8];
-        const uint4 ci = *reinterpret_cast<const uint4 *>(s.cidx + 4 * m);
-        vi[0] = ci.x;
-        vi[1] = ci.y;
-        vi[2] = ci.z;
-        vi[3] = ci.w;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            vi[q] = corner_index(s, g.N + 1, i, j, (int)k, q);
             vi[q + 4] = vi[q] + 1;
             fv[q] = s.vval[vi[q]];
             fv[q + 4] = s.vval[vi[q] + 1];
@@ -1015,13 +1066,17 @@ __global__ void k_refine_select(GridP g, Scratch s) {
     }
 }
 
-__global__ void k_refine_compact(Scratch s) {
+__global__ void k_refine_select(GridP g, Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
+    refine_select(g, s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x,
+                  (unsigned long long)gridDim.x * blockDim.x);
+}
+
+// warps start at w0 and step by stride (multiples of 32)
+__device__ __forceinline__ void refine_compact(const Scratch &s, unsigned long long w0, unsigned long long stride) {
     const unsigned long long V = s.ctr->verts;
     const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long v0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); v0 < V;
-         v0 += stride) {
+    for (unsigned long long v0 = w0; v0 < V; v0 += stride) {
         const unsigned long long v = v0 + lane;
         const bool f = v < V && s.vflag[v];
         const unsigned fm = __ballot_sync(FULL, f);
@@ -1031,6 +1086,12 @@ __global__ void k_refine_compact(Scratch s) {
         base = __shfl_sync(FULL, base, 0);
         if (f) s.rlist[base + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)v;
     }
+}
+
+__global__ void k_refine_compact(Scratch s) {
+    if (s.ctr->flags & STOP_FLAGS) return;
+    refine_compact(s, blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
+                   (unsigned long long)gridDim.x * blockDim.x);
 }
 
 void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st) {
@@ -1099,7 +1160,7 @@ void launch_max_abs_diff(const float *a, const float *b, long long n, unsigned i
 // ---------------------------------------------------------------------------
 // Results: counts, statistics and the status word.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
+__device__ __forceinline__ void finalize(const Scratch &s, const gh_mesh &out, long long columns) {
     const Counters c = *s.ctr;
     long long status = GH_OK;
     if (c.flags & FLAG_NONFINITE) status = GH_ERR_NONFINITE;
@@ -1127,8 +1188,153 @@ __global__ void k_finalize(Scratch s, gh_mesh out, long long columns) {
     }
 }
 
+__global__ void k_finalize(Scratch s, gh_mesh out, long long columns) { finalize(s, out, columns); }
+
 void launch_finalize(Scratch &s, const gh_mesh &out, long long columns, cudaStream_t st) {
     k_finalize<<<1, 1, 0, st>>>(s, out, columns);
+}
+
+// ---------------------------------------------------------------------------
+// Batches: every per-item step as one launch over all items.  A CTA walks the
+// items in order and takes its grid-stride share of each one's work; items
+// whose scratch overflowed are skipped (the host grows it and runs again).
+// ---------------------------------------------------------------------------
+__global__ void k_init_b(const Item *__restrict__ items) {
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(items[blockIdx.x].s.ctr);
+    if (threadIdx.x < sizeof(Counters) / 8) p[threadIdx.x] = 0ull;
+}
+
+void launch_init_b(const Item *items, int n, cudaStream_t st) { k_init_b<<<n, 32, 0, st>>>(items); }
+
+__device__ __forceinline__ bool item_stopped(const Item &it) { return (it.s.ctr->flags & STOP_FLAGS) != 0; }
+
+// which = 0: column counts -> column offsets; 1: line counts -> line offsets (total = vertices)
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce_b(const Item *__restrict__ items, int n, int which) {
+    __shared__ uint32_t wsum[32];
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (item_stopped(it)) continue;
+        const long long N = it.g.N, len = which ? (N + 1) * (N + 1) : N * N;
+        const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+        for (long long t = blockIdx.x; t < nt; t += gridDim.x)
+            scan_reduce_tile(which ? it.s.linecount : it.s.colcount, len, it.s.blocksum, t, wsum);
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply_b(const Item *__restrict__ items, int n, int which) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t prefix;
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (item_stopped(it)) continue;
+        const long long N = it.g.N, len = which ? (N + 1) * (N + 1) : N * N;
+        const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+        for (long long t = blockIdx.x; t < nt; t += gridDim.x)
+            scan_apply_tile(which ? it.s.linecount : it.s.colcount, len, it.s.blocksum,
+                            which ? it.s.lineoff : it.s.coloff, which ? &it.s.ctr->verts : nullptr, t, nt, wsum,
+                            &prefix);
+    }
+}
+
+__global__ void k_scatter_marks_b(const Item *__restrict__ items, int n) {
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (item_stopped(it)) continue;
+        scatter_marks(it.s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x,
+                      (unsigned long long)gridDim.x * blockDim.x);
+    }
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(LINES_T) k_lines_b(const Item *__restrict__ items, int n) {
+    extern __shared__ uint32_t lbits[];
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (item_stopped(it)) continue;
+        lines_pass<EMIT>(it.g, it.s, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                         (long long)gridDim.x * blockDim.x, lbits);
+    }
+}
+
+__global__ void k_check_verts_b(const Item *__restrict__ items, int n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && items[b].s.ctr->verts > (unsigned long long)items[b].s.cap_verts)
+        atomicOr(&items[b].s.ctr->flags, FLAG_VERT_OVERFLOW);
+}
+
+void launch_build_lists_b(const Item *items, int n, int max_N, int nsm, cudaStream_t st) {
+    const int grid = nsm * 2;
+    k_scan_reduce_b<<<grid, SCAN_T, 0, st>>>(items, n, 0);
+    k_scan_apply_b<<<grid, SCAN_T, 0, st>>>(items, n, 0);
+    k_scatter_marks_b<<<nsm * 8, 256, 0, st>>>(items, n);
+    const size_t lsm = (size_t)((max_N + 1 + 31) / 32) * LINES_T * sizeof(uint32_t);
+    k_lines_b<false><<<nsm * 16, LINES_T, lsm, st>>>(items, n);
+    k_scan_reduce_b<<<grid, SCAN_T, 0, st>>>(items, n, 1);
+    k_scan_apply_b<<<grid, SCAN_T, 0, st>>>(items, n, 1);
+    k_check_verts_b<<<(n + 127) / 128, 128, 0, st>>>(items, n);
+    k_lines_b<true><<<nsm * 16, LINES_T, lsm, st>>>(items, n);
+}
+
+__global__ void __launch_bounds__(256) k_eval_vertices_csg_b(const Item *__restrict__ items, int n) {
+    extern __shared__ float4 sprim[];
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (it.kind != GH_SDB_CSG) continue;
+        load_prims(sprim, it.prims, it.nprim);  // ends with __syncthreads
+        if (!item_stopped(it))
+            eval_vertices_csg(sprim, it.nprim, it.g, it.s, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x,
+                              (unsigned long long)gridDim.x * blockDim.x);
+        __syncthreads();  // the next item's primitives replace these only when every thread is done
+    }
+}
+
+void launch_eval_vertices_csg_b(const Item *items, int n, int max_prims, int nsm, cudaStream_t st) {
+    const size_t smem = (size_t)max_prims * sizeof(Prim);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_vertices_csg_b, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_eval_vertices_csg_b<<<nsm * per_sm, 256, smem, st>>>(items, n);
+}
+
+// phase 0: clear the flags, 1: flag the vertices to refine, 2: list them
+__global__ void k_refine_b(const Item *__restrict__ items, int n, int phase) {
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (it.kind != GH_SDB_MLP || item_stopped(it)) continue;
+        const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+        const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+        if (phase == 0) refine_zero(it.s, t0, stride);
+        else if (phase == 1) refine_select(it.g, it.s, t0, stride);
+        else refine_compact(it.s, t0 & ~31ull, stride);
+    }
+}
+
+void launch_refine_select_b(const Item *items, int n, int nsm, cudaStream_t st) {
+    for (int phase = 0; phase < 3; ++phase) k_refine_b<<<nsm * 8, 256, 0, st>>>(items, n, phase);
+}
+
+__global__ void __launch_bounds__(256) k_mc_b(const Item *__restrict__ items, int n) {
+    __shared__ float stage[8][EMIT_STAGE];
+    __shared__ McTab tab;
+    load_tab(tab);
+    for (int b = 0; b < n; ++b) {
+        const Item &it = items[b];
+        if (item_stopped(it)) continue;
+        mc_cells(it.g, it.s, it.out, stage[threadIdx.x >> 5], tab,
+                 blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
+                 (unsigned long long)gridDim.x * blockDim.x);
+    }
+}
+
+void launch_mc_b(const Item *items, int n, int nsm, cudaStream_t st) { k_mc_b<<<nsm * 8, 256, 0, st>>>(items, n); }
+
+__global__ void k_finalize_b(const Item *__restrict__ items, int n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) finalize(items[b].s, items[b].out, (long long)items[b].g.N * items[b].g.N);
+}
+
+void launch_finalize_b(const Item *items, int n, cudaStream_t st) {
+    k_finalize_b<<<(n + 127) / 128, 128, 0, st>>>(items, n);
 }
 
 }  // namespace gh

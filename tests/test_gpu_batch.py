@@ -104,10 +104,13 @@ def test_autotuner_picks_a_candidate(tmp_path):
     assert os.path.exists(tmp_path / "tune.json")
 
 
-def test_full_batch_config_64_items():
+@pytest.mark.parametrize("precision", ["bf16", "bf16x6"])
+def test_full_batch_config_64_items(precision):
     """The 64-item batch (seeds 0..63: even CSG, odd neural of width 64/128/256,
-    N from {128,...,1024}) in BF16 + FP32 refinement: every item equals its
-    single-call result in surface cells and triangles."""
+    N from {128,...,1024}): every item equals its single-call result mesh for
+    mesh (same triangles, bit-identical vertices), and the items with N <= 256
+    match the oracle -- every column for the analytic items and the N = 128
+    neural ones, 256 random columns for the N = 256 neural ones."""
     items = synth.batch_items(64)
     sdbs, Ns = [], []
     for kind, seed, N, W in items:
@@ -116,10 +119,41 @@ def test_full_batch_config_64_items():
             s.calibrate(N, n_points=1 << 18)
         sdbs.append(s)
         Ns.append(N)
-    bt = gh.polygonize_batch(sdbs, Ns, precision="bf16", keys=True)
+    bt = gh.polygonize_batch(sdbs, Ns, precision=precision, keys=True, cells=True)
+    # a fixed number of launches, whatever the number of items: counters, one
+    # hopping launch per evaluator family (analytic, neural widths 64/128/256),
+    # lists (8), vertex values (1 + 3), refinement (3 + 3), Marching Cubes,
+    # status words
+    launches, _ = gh.last_profile()
+    assert launches == 1 + 4 + 8 + 4 + 6 + 1 + 1
+    fam = {}
+    for b, (kind, _, _, W) in enumerate(items):
+        fam.setdefault((kind, W if kind == "mlp" else 0), b)
+    pick = sorted(fam.values())  # one item of each family: the same launches as 64
+    small = gh.polygonize_batch([sdbs[b] for b in pick], [Ns[b] for b in pick], precision=precision)
+    assert gh.last_profile()[0] == launches and small.mesh(0).n_tris > 0
+    checked = 0
     for b, (kind, seed, N, W) in enumerate(items):
-        st = bt.mesh(b).stats
-        single = gh.polygonize(sdbs[b], N, precision="bf16" if kind == "mlp" else "fp32",
+        m = bt.mesh(b)
+        single = gh.polygonize(sdbs[b], N, precision=precision if kind == "mlp" else "fp32",
                                eps=sdbs[b].eps if kind == "mlp" else None, keys=True)
-        assert st["surface_cells"] == single.stats["surface_cells"], (b, kind, N)
-        assert bt.mesh(b).n_tris == single.n_tris
+        _same(m, single, N)
+        assert m.stats["surface_cells"] == single.stats["surface_cells"], (b, kind, N)
+        if N > 256:
+            continue
+        if kind == "csg":
+            o = oracle.csg(synth.csg_prims(seed))
+        else:
+            o = oracle.mlp(W, synth.MLP_NMID, synth.mlp_params(seed, W).astype(np.float64))
+        gprec = precision if kind == "mlp" else "fp32"
+        if kind == "csg" or N == 128:
+            _, ref = oracle.polygonize(o, N)
+            st = parity.compare(m, o, N, ref=ref, gsdb=sdbs[b], gprec=gprec, min_bare=0.995)
+        else:
+            cols = np.random.default_rng(seed).choice(N * N, 256, replace=False)
+            _, ref = oracle.polygonize(o, N, cols=cols)
+            st = parity.compare(m, o, N, ref=ref, restrict_cells=lambda c: np.isin(c // N, cols), gsdb=sdbs[b],
+                                gprec=gprec, min_bare=0.995)
+        assert st["sign_flip_outside_band"] <= 8
+        checked += 1
+    assert checked == 26

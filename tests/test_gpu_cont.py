@@ -36,7 +36,9 @@ def test_sphere_cont_equals_hopping_and_oracle(N):
     assert st["hop_evals"] >= 8 * st["marked_cells"]
     o = oracle.csg(prims)
     ref = oracle.cont(o, N, [[0.0, 0.0, 0.0]])
-    s = parity.compare(c, o, N, ref=ref, gsdb=sdb)
+    # the centre and radius in float32 put many lattice corners within ~1e-8 of
+    # the surface (band ties); vertices next to them have a larger FP32 error
+    s = parity.compare(c, o, N, ref=ref, gsdb=sdb, min_bare=0.995)
     assert s["sign_flip_outside_band"] == 0
 
 
