@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "bf16x6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="time the headline workload only")
+    ap.add_argument("--no-companions", action="store_true",
+                    help="skip the other precisions of the headline workload (for profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--N", type=int, default=None, help="grid size (default 1024; smaller for profiling)")
     ap.add_argument("--workload", default="neural", choices=["neural", "batch", "csg", "adjoint", "crossover"],
@@ -479,7 +481,7 @@ def run_ours(args):
         "roofline": roof, "kernels": kern, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
     ctx = {}
-    if precision != "fp32":
+    if precision != "fp32" and not args.no_companions:
         line["fp32_path"] = companion(gh, torch, sdb, N, bufs, stream, flush, "fp32")
         other = "bf16" if precision == "bf16x6" else "bf16x6"
         line["bf16_fp32_refine_path" if other == "bf16" else "bf16x6_refine_path"] = companion(

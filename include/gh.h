@@ -389,6 +389,18 @@ typedef struct {
 int gh_set_profiling(int enable);
 int gh_last_profile(gh_profile *out);
 
+/* The limit, in nanoseconds, of the bounded waits the neural engines make
+ * on their own work (BF16 and split-BF16 tensor-core engines: one role waiting
+ * for another through an mbarrier; FP32 engine: a weight copy landing).  When
+ * a wait runs out the kernel records it, the BF16 engines' roles leave their
+ * loops (copies in flight land and issued MMAs complete, with a fixed 2 s
+ * limit, before tensor memory is freed) and the FP32 engine records it and
+ * keeps waiting for its copy; the call then reports GH_ERR_CUDA ("a bounded
+ * device wait timed out") and the SDB stays usable.  Default and maximum 2 s
+ * (2e9); 0 makes every wait that is not already satisfied run out at once --
+ * a way to exercise the timeout path.  Process-wide; later launches take it. */
+int gh_set_wait_limit_ns(uint64_t ns);
+
 /* Copies the library's Marching Cubes table to host memory: ntri[256] and
  * edges[256][5][3] (-1 padded).  Host-only; needs no GPU. */
 int gh_mc_table(int32_t *ntri, int32_t *edges);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -37,6 +38,17 @@ static int fail(int code, const char *fmt, ...) {
     } while (0)
 
 extern "C" const char *gh_last_error(void) { return g_err.c_str(); }
+
+// The bounded waits of the neural engines (gh.h: gh_set_wait_limit_ns).
+static std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+unsigned long long gh::wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+extern "C" int gh_set_wait_limit_ns(uint64_t ns) {
+    if (ns > 2000000000ull) return fail(GH_ERR_ARG, "gh_set_wait_limit_ns: %llu ns is above the 2 s maximum",
+                                        (unsigned long long)ns);
+    g_wait_ns.store(ns == 0 ? 0ull : ns, std::memory_order_relaxed);
+    return GH_OK;
+}
 extern "C" const char *gh_version(void) { return "gridhop-gb300 0.1 (sm_103a)"; }
 
 extern "C" int64_t gh_column_order(int32_t N, int64_t c) {
@@ -735,13 +747,14 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         Counters c;
         GH_CUDA(cudaMemcpyAsync(&c, s->scr.ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
         GH_CUDA(cudaStreamSynchronize(st));
+        // a wait that ran out leaves the other counters meaningless
+        if (c.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
         if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) {
             if (c.flags & FLAG_MARK_OVERFLOW) want_m = (long long)(c.marks + c.marks / 4 + 1024);
             want_v = (c.flags & FLAG_VERT_OVERFLOW) ? (long long)(c.verts + c.verts / 4 + 1024) : 2 * want_m;
             if (want_v < 2 * want_m) want_v = 2 * want_m;
             continue;
         }
-        if (c.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
         if (c.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
         if (c.tris > (unsigned long long)out->capacity_tris)
             return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris,
@@ -815,11 +828,11 @@ extern "C" int gh_polygonize_cont(const gh_grid *grid, const gh_sdb *csdb, const
         Counters h;
         GH_CUDA(cudaMemcpyAsync(&h, c.ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
         GH_CUDA(cudaStreamSynchronize(st));
+        if (h.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
         if (h.flags & FLAG_MARK_OVERFLOW) {
             want_m = (long long)(h.marks + h.marks / 4 + 1024);
             continue;
         }
-        if (h.flags & FLAG_TIMEOUT) return fail(GH_ERR_CUDA, "a bounded device wait timed out");
         if (h.flags & FLAG_NONFINITE) return fail(GH_ERR_NONFINITE, "the SDB evaluated to NaN or inf");
         if (h.tris > (unsigned long long)out->capacity_tris)
             return fail(GH_ERR_CAPACITY, "triangle buffer holds %lld, %llu needed", (long long)out->capacity_tris,

@@ -206,6 +206,10 @@ __host__ __device__ inline uint32_t mark_col(unsigned long long m) { return (uin
 __host__ __device__ inline uint32_t mark_k(unsigned long long m) { return (uint32_t)((m >> 24) & 0xFFFFull); }
 __host__ __device__ inline uint32_t mark_rank(unsigned long long m) { return (uint32_t)((m >> 40) & 0xFFFFull); }
 
+// The limit of the engines' bounded waits on their own work, in ns (gh_api.cu;
+// gh_set_wait_limit_ns; 2 s unless set).
+unsigned long long wait_limit_ns();
+
 // ---- launchers implemented in the kernels' translation units ----------------
 cudaError_t upload_mc_table(const int32_t *ntri, const int32_t *edges);  // k_pipeline.cu
 void launch_init(Scratch &s, cudaStream_t st);

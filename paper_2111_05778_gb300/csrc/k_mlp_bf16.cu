@@ -89,7 +89,7 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, floa
 template <int W, int MODE, int TILES>
 __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     k_mlp_bf16(const Item *__restrict__ items, int n_items, const float *__restrict__ pts, long long npts,
-               float *__restrict__ outv) {
+               float *__restrict__ outv, unsigned long long wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int KB = W / 64;
     constexpr uint32_t STAGE_BYTES = W * 128;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     continue;
                 }
                 if (lt[t] == 0) {  // a new step of tile t: its item (or its end) is decided first
-                    if (!wait_bar(&sm.item_ready[t], pir[t], ctl, CTL_ABORT, ctr0)) break;
+                    if (!wait_bar(&sm.item_ready[t], pir[t], ctl, CTL_ABORT, ctr0, wait_ns)) break;
                     pir[t] ^= 1u;
                     if (vdone[t]) {
                         fin[t] = true;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(issued % NSTAGE);
                     const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
-                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0)) {
+                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
                         go = false;
                         break;
                     }
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     t ^= 1;
                     continue;
                 }
-                if (!wait_bar(&sm.a_full[t], pa[t], ctl, CTL_ABORT, ctr0)) break;
+                if (!wait_bar(&sm.a_full[t], pa[t], ctl, CTL_ABORT, ctr0, wait_ns)) break;
                 pa[t] ^= 1u;
                 if (lt[t] == 0 && vdone[t]) {
                     fin[t] = true;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 const uint32_t at = su32(&sm.a[t][0][0]);
                 for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(consumed % NSTAGE);
-                    if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0)) {
+                    if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0, wait_ns)) {
                         go = false;
                         break;
                     }
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             // 3. hidden layers
             float gsum = 0.f;
             for (int l = 0; l < n_mid; ++l) {
-                wait_bar(&sm.acc_full[t], pacc, ctl, CTL_ABORT, ctr0);
+                wait_bar(&sm.acc_full[t], pacc, ctl, CTL_ABORT, ctr0, wait_ns);
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
@@ -555,7 +555,7 @@ void launch_bf16(const Item *items, int n_items, const float *p, long long n, fl
         const long long tiles = (n + 128 * TILES - 1) / (128 * TILES);
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
     }
-    k_mlp_bf16<W, MODE, TILES><<<grid, 128 + 128 * TILES, smem, st>>>(items, n_items, p, n, out);
+    k_mlp_bf16<W, MODE, TILES><<<grid, 128 + 128 * TILES, smem, st>>>(items, n_items, p, n, out, wait_limit_ns());
 }
 
 }  // namespace

@@ -41,7 +41,8 @@ struct Smem {
     float red[TM];
     unsigned long long full[2];  // chunk landed in buffer b (complete_tx)
     unsigned int done[2];        // warps finished with buffer b
-    int abort;                   // a chunk wait timed out: stop waiting
+    int abort;                   // a chunk wait gave up after 2 s: stop waiting
+    unsigned long long wait_ns;  // the caller's wait limit (gh_set_wait_limit_ns)
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -62,19 +63,30 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
     return ok != 0;
 }
 
-// waits for the phase of the given parity of buffer b's barrier; after 2 s
-// sets the abort bit (later waits return at once) and the timeout flag
+// Waits for the phase of the given parity of buffer b's barrier.  What it
+// waits for is one of this CTA's own bulk copies, which lands: at the caller's
+// limit (sm.wait_ns) the timeout is recorded in the device flags and the wait
+// goes on, so that no copy is ever left in flight; only after 2 s does it set
+// the abort bit (later waits return at once) and return.
 template <int W>
 __device__ __noinline__ void wait_chunk(Smem<W> &sm, int b, uint32_t parity, Counters *ctr) {
     if (mbar_try(&sm.full[b], parity)) return;
-    const unsigned long long t0 = gtimer();
+    const unsigned long long t0 = gtimer(), lim = sm.wait_ns;
+    bool flagged = false;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(&sm.full[b], parity)) return;
         if (*(volatile int *)&sm.abort) return;
-        if ((it & 255) == 0 && gtimer() - t0 > WAIT_NS) {
-            atomicOr((int *)&sm.abort, 1);
-            atomicOr(&ctr->flags, FLAG_TIMEOUT);
-            return;
+        if ((it & 255) == 0 || lim < 100000ull) {
+            const unsigned long long dt = gtimer() - t0;
+            if (!flagged && dt > lim) {
+                atomicOr(&ctr->flags, FLAG_TIMEOUT);
+                flagged = true;
+            }
+            if (dt > WAIT_NS) {
+                atomicOr((int *)&sm.abort, 1);
+                atomicOr(&ctr->flags, FLAG_TIMEOUT);
+                return;
+            }
         }
     }
 }
@@ -106,13 +118,14 @@ __device__ __forceinline__ void issue_chunk(const MlpDev &m, Smem<W> &sm, int ch
 
 // once per CTA, before its first tile
 template <int W>
-__device__ __forceinline__ void init_ring(Smem<W> &sm) {
+__device__ __forceinline__ void init_ring(Smem<W> &sm, unsigned long long wait_ns) {
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sm.full[b])) : "memory");
             sm.done[b] = 0;
         }
         sm.abort = 0;
+        sm.wait_ns = wait_ns;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -290,12 +303,13 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float4 p, float g) {
 // from item cur's queue; when the item has no column left for this CTA and
 // all rows are done, the CTA moves to the next item.
 template <int W>
-__global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__ items, int n_items) {
+__global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__ items, int n_items,
+                                                         unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    init_ring<W>(sm);
+    init_ring<W>(sm, wait_ns);
     uint32_t ph[2] = {0u, 0u};
     int cur = 0;
     uint32_t col = NONE, rank = 0;
@@ -405,13 +419,14 @@ __global__ void __launch_bounds__(NT, 1) k_hop_mlp_fp32(const Item *__restrict__
 // (one item), MODE 3 = all (N+1)^3 lattice points into s.lat (enumeration).
 template <int W, int MODE>
 __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__ items, int n_items,
-                                                         const float *pts, long long npts, float *outv) {
+                                                         const float *pts, long long npts, float *outv,
+                                                         unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     __shared__ unsigned long long tile_s;
     __shared__ unsigned long long total_s;
     const int tid = threadIdx.x;
-    init_ring<W>(sm);
+    init_ring<W>(sm, wait_ns);
     uint32_t ph[2] = {0u, 0u};
     for (int cur = 0; cur < n_items;) {
         const Item &it = items[cur];
@@ -476,11 +491,11 @@ __global__ void __launch_bounds__(NT, 1) k_pts_mlp_fp32(const Item *__restrict__
 template <int W>
 __global__ void __launch_bounds__(NT, 1) k_adj_fwd(MlpDev m, const float *__restrict__ P, long long V,
                                                    float *__restrict__ Z, long long ldl, uint32_t *__restrict__ mbits,
-                                                   Counters *ctr) {
+                                                   Counters *ctr, unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     const int tid = threadIdx.x;
-    init_ring<W>(sm);
+    init_ring<W>(sm, wait_ns);
     uint32_t ph[2] = {0u, 0u};
     for (long long t = blockIdx.x; t * TM < V; t += gridDim.x) {
         const long long row0 = t * TM;
@@ -497,11 +512,12 @@ __global__ void __launch_bounds__(NT, 1) k_adj_fwd(MlpDev m, const float *__rest
 // delta_0, masked by the stored pre-activations Z, into D.
 template <int W>
 __global__ void __launch_bounds__(NT, 1) k_adj_bwd(MlpDev m, long long V, const uint32_t *__restrict__ mbits,
-                                                   float *__restrict__ D, long long ldl, Counters *ctr) {
+                                                   float *__restrict__ D, long long ldl, Counters *ctr,
+                                                   unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<W> &sm = *reinterpret_cast<Smem<W> *>(smem_raw);
     const int tid = threadIdx.x;
-    init_ring<W>(sm);
+    init_ring<W>(sm, wait_ns);
     uint32_t ph[2] = {0u, 0u};
     const float *DL = D + (size_t)m.n_mid * ldl;
     for (long long t = blockIdx.x; t * TM < V; t += gridDim.x) {
@@ -544,7 +560,7 @@ void launch_hop_mlp_fp32(const Item *items, int n_items, int width, int nsm, cud
     GH_DISPATCH_W(width, {
         const size_t smem = sizeof(Smem<WW>);
         const int grid = occupancy_grid(k_hop_mlp_fp32<WW>, smem, nsm);
-        k_hop_mlp_fp32<WW><<<grid, NT, smem, st>>>(items, n_items);
+        k_hop_mlp_fp32<WW><<<grid, NT, smem, st>>>(items, n_items, wait_limit_ns());
     })
 }
 
@@ -554,10 +570,10 @@ void launch_eval_vertices_mlp_fp32(const Item *items, int n_items, int width, in
         const size_t smem = sizeof(Smem<WW>);
         if (refine_list) {
             const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 1>, smem, nsm);
-            k_pts_mlp_fp32<WW, 1><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr);
+            k_pts_mlp_fp32<WW, 1><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr, wait_limit_ns());
         } else {
             const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 0>, smem, nsm);
-            k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr);
+            k_pts_mlp_fp32<WW, 0><<<grid, NT, smem, st>>>(items, n_items, nullptr, 0, nullptr, wait_limit_ns());
         }
     })
 }
@@ -566,7 +582,7 @@ void launch_lattice_mlp_fp32(const Item *items, int width, int nsm, cudaStream_t
     GH_DISPATCH_W(width, {
         const size_t smem = sizeof(Smem<WW>);
         const int grid = occupancy_grid(k_pts_mlp_fp32<WW, 3>, smem, nsm);
-        k_pts_mlp_fp32<WW, 3><<<grid, NT, smem, st>>>(items, 1, nullptr, 0, nullptr);
+        k_pts_mlp_fp32<WW, 3><<<grid, NT, smem, st>>>(items, 1, nullptr, 0, nullptr, wait_limit_ns());
     })
 }
 
@@ -587,7 +603,7 @@ void launch_adj_fwd_fp32(const MlpDev &m, const float *P, long long V, float *Z,
         int grid = occupancy_grid(k_adj_fwd<WW>, smem, nsm);
         const long long tiles = (V + TM - 1) / TM;
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
-        k_adj_fwd<WW><<<grid, NT, smem, st>>>(m, P, V, Z, ldl, mbits, ctr);
+        k_adj_fwd<WW><<<grid, NT, smem, st>>>(m, P, V, Z, ldl, mbits, ctr, wait_limit_ns());
     })
 }
 
@@ -599,7 +615,7 @@ void launch_adj_bwd_fp32(const MlpDev &m, long long V, const uint32_t *mbits, fl
         int grid = occupancy_grid(k_adj_bwd<WW>, smem, nsm);
         const long long tiles = (V + TM - 1) / TM;
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
-        k_adj_bwd<WW><<<grid, NT, smem, st>>>(m, V, mbits, D, ldl, ctr);
+        k_adj_bwd<WW><<<grid, NT, smem, st>>>(m, V, mbits, D, ldl, ctr, wait_limit_ns());
     })
 }
 
@@ -621,7 +637,7 @@ void launch_eval_points_mlp_fp32(const MlpDev &m, const float *p, long long n, f
         int grid = occupancy_grid(k_pts_mlp_fp32<WW, 2>, smem, nsm);
         const long long tiles = (n + TM - 1) / TM;
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
-        k_pts_mlp_fp32<WW, 2><<<grid, NT, smem, st>>>(ditem, 1, p, n, out);
+        k_pts_mlp_fp32<WW, 2><<<grid, NT, smem, st>>>(ditem, 1, p, n, out, wait_limit_ns());
     })
 }
 

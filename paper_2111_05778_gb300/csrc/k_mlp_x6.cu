@@ -99,7 +99,7 @@ __device__ __forceinline__ void load_params(SmemX<W> &sm, const MlpDev &mm, int 
 template <int W, int MODE>
 __global__ void __launch_bounds__(384, 1)
     k_mlp_x6(const Item *__restrict__ items, int n_items, const float *__restrict__ pts, long long npts,
-             float *__restrict__ outv) {
+             float *__restrict__ outv, unsigned long long wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int KB = W / 64;                 // K-blocks per layer
     constexpr uint32_t STAGE_BYTES = W * 128;  // one K-block of one part
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(384, 1)
             uint32_t pir = 0;
             bool go = true;
             while (go) {
-                if (!wait_bar(&sm.item_ready, pir, ctl, CTL_ABORT, ctr0)) break;
+                if (!wait_bar(&sm.item_ready, pir, ctl, CTL_ABORT, ctr0, wait_ns)) break;
                 pir ^= 1u;
                 if (*vdone) break;
                 const uint8_t *src = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_w);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(384, 1)
                 for (int s = 0; s < nst; ++s) {
                     const int st = (int)(issued % NST);
                     const uint32_t par = (uint32_t)(((issued / NST) & 1) ^ 1);
-                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0)) {
+                    if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
                         go = false;
                         break;
                     }
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(384, 1)
             const uint32_t ah0 = su32(&sm.ah[0][0]);
             while (go) {
                 for (int l = 0; l < n_mid && go; ++l) {
-                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, ctr0)) {
+                    if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, ctr0, wait_ns)) {
                         go = false;
                         break;
                     }
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(384, 1)
                     for (int part = 0; part < 3 && go; ++part) {  // weight parts low, middle, high
                         for (int kb = 0; kb < KB; ++kb) {
                             const int st = (int)(consumed % NST);
-                            if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NST) & 1), ctl, CTL_ABORT, ctr0)) {
+                            if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NST) & 1), ctl, CTL_ABORT, ctr0, wait_ns)) {
                                 go = false;
                                 break;
                             }
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(384, 1)
             //    and after the last one the output dot product
             float gs = 0.f;
             for (int l = 0; l < n_mid; ++l) {
-                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, ctr0);
+                wait_bar(&sm.acc_full, pacc, ctl, CTL_ABORT, ctr0, wait_ns);
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
@@ -395,7 +395,7 @@ void launch_x6(const Item *items, int n_items, const float *p, long long n, floa
         const long long tiles = (n + TM - 1) / TM;
         if (grid > tiles) grid = (int)(tiles < 1 ? 1 : tiles);
     }
-    k_mlp_x6<W, MODE><<<grid, 384, smem, st>>>(items, n_items, p, n, out);
+    k_mlp_x6<W, MODE><<<grid, 384, smem, st>>>(items, n_items, p, n, out, wait_limit_ns());
 }
 
 }  // namespace

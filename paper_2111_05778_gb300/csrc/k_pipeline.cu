@@ -648,8 +648,16 @@ constexpr int EMIT_STAGE = 32 * 5 * 9;
 // puts its vertex positions at its offset in the warp's staging buffer, and
 // the warp then writes the range with consecutive lanes on consecutive
 // floats (coalesced stores).
+// Per-block slots for claiming output ranges with one atomic per block
+// instead of one per warp (the counters are single addresses every warp of
+// the grid would otherwise hit).
+struct BlockSlots {
+    unsigned long long t[8], c[8], tb[8], cb[8], base_t, base_c;
+};
+
 __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const gh_mesh &out, bool valid, int i, int j,
-                                           int k, const float (&fv)[8], float *stage, const McTab &tab) {
+                                           int k, const float (&fv)[8], float *stage, const McTab &tab,
+                                           BlockSlots *bs = nullptr) {
     const int N = g.N, N1 = N + 1;
     const unsigned long long N13 = (unsigned long long)N1 * N1 * N1;
     const int lane = threadIdx.x & 31;
@@ -668,17 +676,42 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
         if (lane >= o) x += y;
     }
     const int wtot = __shfl_sync(FULL, x, 31);
-    unsigned long long wbase = 0;
-    if (wtot) {
-        if (lane == 31) wbase = atomicAdd(&ctr->tris, (unsigned long long)wtot);
-        wbase = __shfl_sync(FULL, wbase, 31);
+    const unsigned sm = __ballot_sync(FULL, surf);
+    unsigned long long wbase = 0, cbase = 0;
+    if (bs) {
+        // the whole block calls: one atomic per counter for all its warps
+        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if (lane == 0) {
+            bs->t[w] = (unsigned long long)wtot;
+            bs->c[w] = (unsigned long long)__popc(sm);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tt = 0, cc = 0;
+            for (int q = 0; q < nw; ++q) {
+                bs->tb[q] = tt;
+                tt += bs->t[q];
+                bs->cb[q] = cc;
+                cc += bs->c[q];
+            }
+            bs->base_t = tt ? atomicAdd(&ctr->tris, tt) : 0ull;
+            bs->base_c = cc ? atomicAdd(&ctr->cells, cc) : 0ull;
+        }
+        __syncthreads();
+        wbase = bs->base_t + bs->tb[w];
+        cbase = bs->base_c + bs->cb[w];
+    } else {
+        if (wtot) {
+            if (lane == 31) wbase = atomicAdd(&ctr->tris, (unsigned long long)wtot);
+            wbase = __shfl_sync(FULL, wbase, 31);
+        }
+        if (sm) {
+            if (lane == 0) cbase = atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
+            cbase = __shfl_sync(FULL, cbase, 0);
+        }
     }
     const int loc = x - nt;  // this lane's first triangle within the warp's range
-    const unsigned sm = __ballot_sync(FULL, surf);
     if (sm && out.cell_ids) {
-        unsigned long long cbase = 0;
-        if (lane == 0) cbase = atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
-        cbase = __shfl_sync(FULL, cbase, 0);
         if (surf) {
             const unsigned long long ci = cbase + __popc(sm & lt);
             if (ci < (unsigned long long)out.capacity_cells) {
@@ -686,8 +719,6 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
                 out.cell_cases[ci] = (uint8_t)cs;
             }
         }
-    } else if (sm && lane == 0) {
-        atomicAdd(&ctr->cells, (unsigned long long)__popc(sm));
     }
     if (!wtot) return;
     for (int t = 0; t < nt; ++t) {
@@ -731,15 +762,15 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
     __syncwarp();  // the buffer is free for the warp's next cells
 }
 
-// Marching Cubes on the marked cells; warps start at w0 (a multiple of 32)
-// and step by stride (a multiple of 32).
+// Marching Cubes on the marked cells; the whole block calls, its cells start
+// at b0 and step by stride (multiples of the block size).
 __device__ __forceinline__ void mc_cells(const GridP &g, const Scratch &s, const gh_mesh &out, float *stage,
-                                         const McTab &tab, unsigned long long w0, unsigned long long stride) {
+                                         const McTab &tab, BlockSlots *bs, unsigned long long b0,
+                                         unsigned long long stride) {
     const unsigned long long M = s.ctr->marks;
     const int N = g.N;
-    const int lane = threadIdx.x & 31;
-    for (unsigned long long m0 = w0; m0 < M; m0 += stride) {
-        const unsigned long long m = m0 + lane;
+    for (unsigned long long mb = b0; mb < M; mb += stride) {
+        const unsigned long long m = mb + threadIdx.x;
         const unsigned long long r = m < M ? s.marks_csr[m] : MARK_EMPTY;
         const bool valid = !mark_empty(r);  // cells marked empty have no triangles
         float fv[8];
@@ -756,16 +787,17 @@ __device__ __forceinline__ void mc_cells(const GridP &g, const Scratch &s, const
                 fv[q + 4] = s.vval[idx + 1];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage, tab);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage, tab, bs);
     }
 }
 
 __global__ void __launch_bounds__(256) k_mc(GridP g, Scratch s, gh_mesh out) {
     __shared__ float stage[8][EMIT_STAGE];
     __shared__ McTab tab;
+    __shared__ BlockSlots bs;
     if (s.ctr->flags & STOP_FLAGS) return;
     load_tab(tab);
-    mc_cells(g, s, out, stage[threadIdx.x >> 5], tab, blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
+    mc_cells(g, s, out, stage[threadIdx.x >> 5], tab, &bs, blockIdx.x * (unsigned long long)blockDim.x,
              (unsigned long long)gridDim.x * blockDim.x);
 }
 
@@ -794,12 +826,12 @@ void launch_lattice_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s
 __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh out) {
     __shared__ float stage[8][EMIT_STAGE];
     __shared__ McTab tab;
+    __shared__ BlockSlots bs;
     load_tab(tab);
     const long long N = g.N, N1 = N + 1, n = N * N * N;
-    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long m0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); m0 < n; m0 += stride) {
-        const long long m = m0 + lane;
+    for (long long mb = blockIdx.x * (long long)blockDim.x; mb < n; mb += stride) {
+        const long long m = mb + threadIdx.x;
         const bool valid = m < n;
         float fv[8];
         int i = 0, j = 0, k = 0;
@@ -813,7 +845,7 @@ __global__ void __launch_bounds__(256) k_mc_dense(GridP g, Scratch s, gh_mesh ou
                 fv[b] = s.lat[a + N1 * (bb + N1 * c)];
             }
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5], tab);
+        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5], tab, &bs);
     }
 }
 
@@ -1072,26 +1104,37 @@ __global__ void k_refine_select(GridP g, Scratch s) {
                   (unsigned long long)gridDim.x * blockDim.x);
 }
 
-// warps start at w0 and step by stride (multiples of 32)
-__device__ __forceinline__ void refine_compact(const Scratch &s, unsigned long long w0, unsigned long long stride) {
+// The vertices flagged for refinement, listed; the whole block calls, its
+// vertices start at b0 and step by stride (multiples of the block size); one
+// atomic per block claims the block's slots.
+__device__ __forceinline__ void refine_compact(const Scratch &s, unsigned long long b0, unsigned long long stride) {
+    __shared__ unsigned int wcnt[32], wbase[32];
+    __shared__ unsigned long long bbase;
     const unsigned long long V = s.ctr->verts;
-    const int lane = threadIdx.x & 31;
-    for (unsigned long long v0 = w0; v0 < V; v0 += stride) {
-        const unsigned long long v = v0 + lane;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (unsigned long long vb = b0; vb < V; vb += stride) {
+        const unsigned long long v = vb + threadIdx.x;
         const bool f = v < V && s.vflag[v];
         const unsigned fm = __ballot_sync(FULL, f);
-        if (!fm) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&s.ctr->refine, (unsigned long long)__popc(fm));
-        base = __shfl_sync(FULL, base, 0);
-        if (f) s.rlist[base + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)v;
+        if (lane == 0) wcnt[w] = (unsigned)__popc(fm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int t = 0;
+            for (int q = 0; q < nw; ++q) {
+                wbase[q] = t;
+                t += wcnt[q];
+            }
+            bbase = t ? atomicAdd(&s.ctr->refine, (unsigned long long)t) : 0ull;
+        }
+        __syncthreads();
+        if (f) s.rlist[bbase + wbase[w] + __popc(fm & ((1u << lane) - 1u))] = (uint32_t)v;
+        __syncthreads();  // the slots are rewritten by the next round
     }
 }
 
 __global__ void k_refine_compact(Scratch s) {
     if (s.ctr->flags & STOP_FLAGS) return;
-    refine_compact(s, blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
-                   (unsigned long long)gridDim.x * blockDim.x);
+    refine_compact(s, blockIdx.x * (unsigned long long)blockDim.x, (unsigned long long)gridDim.x * blockDim.x);
 }
 
 void launch_refine_select(const GridP &g, Scratch &s, cudaStream_t st) {
@@ -1164,12 +1207,12 @@ __device__ __forceinline__ void finalize(const Scratch &s, const gh_mesh &out, l
     const Counters c = *s.ctr;
     long long status = GH_OK;
     if (c.flags & FLAG_NONFINITE) status = GH_ERR_NONFINITE;
-    if (c.flags & FLAG_TIMEOUT) status = GH_ERR_CUDA;
     if (c.flags & (FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW)) status = GH_ERR_CAPACITY;
     if (c.tris > (unsigned long long)out.capacity_tris) status = GH_ERR_CAPACITY;
     if (out.cell_ids && c.cells > (unsigned long long)out.capacity_cells) status = GH_ERR_CAPACITY;
     if (out.vert_xyz && c.mesh_verts > (unsigned long long)out.capacity_verts) status = GH_ERR_CAPACITY;
     if (c.flags & FLAG_INDEX_MISS) status = GH_ERR_CUDA;
+    if (c.flags & FLAG_TIMEOUT) status = GH_ERR_CUDA;  // the other counters are then meaningless
     if (out.n_tris) *out.n_tris = (long long)c.tris;
     if (out.n_verts) *out.n_verts = (long long)c.mesh_verts;
     if (out.n_cells) *out.n_cells = (long long)c.cells;
@@ -1305,7 +1348,7 @@ __global__ void k_refine_b(const Item *__restrict__ items, int n, int phase) {
         const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
         if (phase == 0) refine_zero(it.s, t0, stride);
         else if (phase == 1) refine_select(it.g, it.s, t0, stride);
-        else refine_compact(it.s, t0 & ~31ull, stride);
+        else refine_compact(it.s, blockIdx.x * (unsigned long long)blockDim.x, stride);
     }
 }
 
@@ -1316,12 +1359,12 @@ void launch_refine_select_b(const Item *items, int n, int nsm, cudaStream_t st) 
 __global__ void __launch_bounds__(256) k_mc_b(const Item *__restrict__ items, int n) {
     __shared__ float stage[8][EMIT_STAGE];
     __shared__ McTab tab;
+    __shared__ BlockSlots bs;
     load_tab(tab);
     for (int b = 0; b < n; ++b) {
         const Item &it = items[b];
         if (item_stopped(it)) continue;
-        mc_cells(it.g, it.s, it.out, stage[threadIdx.x >> 5], tab,
-                 blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u),
+        mc_cells(it.g, it.s, it.out, stage[threadIdx.x >> 5], tab, &bs, blockIdx.x * (unsigned long long)blockDim.x,
                  (unsigned long long)gridDim.x * blockDim.x);
     }
 }

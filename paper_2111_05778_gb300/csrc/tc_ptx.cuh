@@ -44,16 +44,18 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
 }
 
 // Waits for the phase of the given parity.  Returns false without waiting
-// further once (ctl & give_up) is set; on a 2 s timeout sets the abort bit
-// and the device error flag and returns false.
+// further once (ctl & give_up) is set; after limit_ns nanoseconds sets the
+// abort bit and the device error flag and returns false.  The waits of the
+// engines' work take the caller's limit (gh_set_wait_limit_ns, default 2 s);
+// the drains before exit (copies in flight, MMAs issued) always take 2 s.
 __device__ __noinline__ bool wait_bar(unsigned long long *b, uint32_t parity, volatile int *ctl, int give_up,
-                                      Counters *ctr) {
+                                      Counters *ctr, unsigned long long limit_ns = WAIT_NS) {
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(b, parity)) return true;
         if (*ctl & give_up) return false;
-        if ((it & 255) == 0 && gtimer() - t0 > WAIT_NS) {
+        if (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns) {
             atomicOr((int *)ctl, CTL_ABORT);
             atomicOr(&ctr->flags, FLAG_TIMEOUT);
             return false;

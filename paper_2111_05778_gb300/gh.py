@@ -109,6 +109,7 @@ def lib():
                 "gh_last_profile": (ctypes.c_int, [ctypes.POINTER(Profile)]),
                 "gh_release_cache": (ctypes.c_int, []),
                 "gh_column_order": (I64, [I32, I64]),
+                "gh_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_uint64]),
                 "gh_polygonize_cont": (ctypes.c_int, [ctypes.POINTER(Grid), P, P, I32, ctypes.POINTER(Options),
                                                       ctypes.POINTER(MeshDesc), P]),
             }
@@ -125,7 +126,8 @@ def exported_symbols():
     return ["gh_create_sdb", "gh_destroy_sdb", "gh_sdb_calibrate", "gh_polygonize", "gh_polygonize_batch",
             "gh_backward", "gh_eval", "gh_mc_table", "gh_mlp_param_count", "gh_last_error", "gh_version",
             "gh_set_profiling", "gh_last_profile", "gh_polygonize_csg_noalloc", "gh_batch_graph_launch",
-            "gh_batch_graph_free", "gh_release_cache", "gh_column_order", "gh_polygonize_cont"]
+            "gh_batch_graph_free", "gh_release_cache", "gh_column_order", "gh_polygonize_cont",
+            "gh_set_wait_limit_ns"]
 
 
 def check(rc):
@@ -522,6 +524,12 @@ def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):
     check(lib().gh_eval(sdb.handle, p.data_ptr(), p.shape[0], out.data_ptr(), PRECISIONS[precision],
                         _stream_ptr(stream)))
     return out
+
+
+def set_wait_limit_ns(ns: int):
+    """gh_set_wait_limit_ns: limit of the neural engines' bounded waits (2e9 =
+    2 s, the default; 0 = every wait not already satisfied runs out)."""
+    check(lib().gh_set_wait_limit_ns(int(ns)))
 
 
 def release_cache():

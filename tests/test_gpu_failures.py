@@ -86,3 +86,29 @@ def test_batch_rejects_grids_outside_the_range():
     # and the same SDBs still run
     bt = gh.polygonize_batch(sdbs, [64, 2])
     assert bt.mesh(0).n_tris > 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x6"])
+def test_bounded_wait_runs_out_then_recovers(precision):
+    """Every wait of the neural engines is bounded: with the limit at 0 the
+    first wait not already satisfied runs out, the kernel records it and
+    leaves (tensor-core engines: every role, after its copies land and its
+    MMAs complete; FP32 engine: it keeps waiting for its own copy), the call
+    reports GH_ERR_CUDA, and the next call with the normal limit on the same
+    SDB gives the same mesh as before."""
+    sdb = gh.MlpSdb(synth.mlp_params(1, 128), 128)
+    eps = sdb.calibrate(96) if precision != "fp32" else None
+    ref = gh.polygonize(sdb, 96, precision=precision, eps=eps, keys=True)
+    gh.set_wait_limit_ns(0)
+    try:
+        with pytest.raises(gh.GhError) as e:
+            gh.polygonize(sdb, 96, precision=precision, eps=eps, keys=True)
+        assert e.value.code == gh.GH_ERR_CUDA and "timed out" in str(e.value)
+    finally:
+        gh.set_wait_limit_ns(2_000_000_000)
+    m = gh.polygonize(sdb, 96, precision=precision, eps=eps, keys=True)
+    assert np.array_equal(meshutil.canonical_tris(m.tri_keys.cpu().numpy()),
+                          meshutil.canonical_tris(ref.tri_keys.cpu().numpy()))
+    with pytest.raises(gh.GhError) as e:
+        gh.set_wait_limit_ns(3_000_000_000)
+    assert e.value.code == gh.GH_ERR_ARG
