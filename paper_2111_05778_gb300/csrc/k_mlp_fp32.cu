@@ -78,7 +78,7 @@ __device__ __noinline__ void wait_chunk(Smem<W> &sm, int b, uint32_t parity, Cou
         if (*(volatile int *)&sm.abort) return;
         if ((it & 255) == 0 || lim < 100000ull) {
             const unsigned long long dt = gtimer() - t0;
-            if (!flagged && dt > lim) {
+            if (!flagged && (dt > lim || lim == 0)) {
                 atomicOr(&ctr->flags, FLAG_TIMEOUT);
                 flagged = true;
             }

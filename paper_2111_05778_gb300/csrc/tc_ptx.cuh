@@ -55,7 +55,7 @@ __device__ __noinline__ bool wait_bar(unsigned long long *b, uint32_t parity, vo
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(b, parity)) return true;
         if (*ctl & give_up) return false;
-        if (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns) {
+        if (limit_ns == 0 || (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns)) {
             atomicOr((int *)ctl, CTL_ABORT);
             atomicOr(&ctr->flags, FLAG_TIMEOUT);
             return false;
