@@ -397,8 +397,8 @@ int gh_last_profile(gh_profile *out);
  * limit, before tensor memory is freed) and the FP32 engine records it and
  * keeps waiting for its copy; the call then reports GH_ERR_CUDA ("a bounded
  * device wait timed out") and the SDB stays usable.  Default and maximum 2 s
- * (2e9); 0 makes every wait that is not already satisfied run out at once --
- * a way to exercise the timeout path.  Process-wide; later launches take it. */
+ * (2e9); 0 makes every such wait run out at once, satisfied or not -- a way
+ * to exercise the timeout path.  Process-wide; later launches take it. */
 int gh_set_wait_limit_ns(uint64_t ns);
 
 /* Copies the library's Marching Cubes table to host memory: ntri[256] and

@@ -70,15 +70,20 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
 // the abort bit (later waits return at once) and return.
 template <int W>
 __device__ __noinline__ void wait_chunk(Smem<W> &sm, int b, uint32_t parity, Counters *ctr) {
-    if (mbar_try(&sm.full[b], parity)) return;
-    const unsigned long long t0 = gtimer(), lim = sm.wait_ns;
+    const unsigned long long lim = sm.wait_ns;
     bool flagged = false;
+    if (lim == 0) {  // a limit of 0: the wait counts as run out at once (the timeout path's test device)
+        atomicOr(&ctr->flags, FLAG_TIMEOUT);
+        flagged = true;
+    }
+    if (mbar_try(&sm.full[b], parity)) return;
+    const unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(&sm.full[b], parity)) return;
         if (*(volatile int *)&sm.abort) return;
         if ((it & 255) == 0 || lim < 100000ull) {
             const unsigned long long dt = gtimer() - t0;
-            if (!flagged && (dt > lim || lim == 0)) {
+            if (!flagged && dt > lim) {
                 atomicOr(&ctr->flags, FLAG_TIMEOUT);
                 flagged = true;
             }

@@ -953,6 +953,7 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
         int n = 0;
         if (lane == 0) {
             const unsigned long long t0 = gtimer_ns();
+            unsigned nap = 32;  // an idle warp backs off, so that the few with work are not starved
             for (unsigned it = 1;; ++it) {
                 h = vc->q_head;
                 unsigned long long t = vc->marks;
@@ -966,10 +967,12 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
                     continue;
                 }
                 if (vc->q_pending == 0ull || (vc->flags & FLAG_TIMEOUT)) break;
-                if ((it & 63u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
+                if ((it & 15u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
                     atomicOr(&s.ctr->flags, FLAG_TIMEOUT);
                     break;
                 }
+                __nanosleep(nap);
+                nap = nap < 1024u ? 2u * nap : 1024u;
             }
         }
         n = __shfl_sync(FULL, n, 0);
@@ -1040,10 +1043,8 @@ void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, c
     cudaMemsetAsync(s.vis, 0, sizeof(uint32_t) * ((ncell + 31) / 32), st);
     k_cont_seed<<<(n_seeds + 127) / 128, 128, smem, st>>>(prims, nprim, g, s, seeds, n_seeds);
     cudaFuncSetAttribute(k_cont_csg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cont_csg, 256, smem);
-    if (per_sm < 1) per_sm = 1;
-    k_cont_csg<<<nsm * per_sm, 256, smem, st>>>(prims, nprim, g, s, out);
+    // one CTA (8 warps) per SM: the crawl's front holds a few thousand cells
+    k_cont_csg<<<nsm, 256, smem, st>>>(prims, nprim, g, s, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -50,12 +50,17 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
 // the drains before exit (copies in flight, MMAs issued) always take 2 s.
 __device__ __noinline__ bool wait_bar(unsigned long long *b, uint32_t parity, volatile int *ctl, int give_up,
                                       Counters *ctr, unsigned long long limit_ns = WAIT_NS) {
+    if (limit_ns == 0) {  // a limit of 0: the wait runs out at once (the timeout path's test device)
+        atomicOr((int *)ctl, CTL_ABORT);
+        atomicOr(&ctr->flags, FLAG_TIMEOUT);
+        return false;
+    }
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(b, parity)) return true;
         if (*ctl & give_up) return false;
-        if (limit_ns == 0 || (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns)) {
+        if (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns) {
             atomicOr((int *)ctl, CTL_ABORT);
             atomicOr(&ctr->flags, FLAG_TIMEOUT);
             return false;

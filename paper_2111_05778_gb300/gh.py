@@ -528,7 +528,7 @@ def eval_points(sdb: Sdb, pts, precision="fp32", stream=None):
 
 def set_wait_limit_ns(ns: int):
     """gh_set_wait_limit_ns: limit of the neural engines' bounded waits (2e9 =
-    2 s, the default; 0 = every wait not already satisfied runs out)."""
+    2 s, the default; 0 = every wait on the engines' own work runs out at once)."""
     check(lib().gh_set_wait_limit_ns(int(ns)))
 
 

@@ -90,8 +90,8 @@ def test_batch_rejects_grids_outside_the_range():
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x6"])
 def test_bounded_wait_runs_out_then_recovers(precision):
-    """Every wait of the neural engines is bounded: with the limit at 0 the
-    first wait not already satisfied runs out, the kernel records it and
+    """Every wait of the neural engines is bounded: with the limit at 0 every
+    wait on the engines' own work runs out at once, the kernel records it and
     leaves (tensor-core engines: every role, after its copies land and its
     MMAs complete; FP32 engine: it keeps waiting for its own copy), the call
     reports GH_ERR_CUDA, and the next call with the normal limit on the same
