@@ -237,10 +237,14 @@ int gh_release_cache(void);
 
 /* Measures the BF16 evaluation error of a neural SDB (the reduced-precision
  * counterpart of the paper's shrink factor lambda, Sec. 5.2): eps = 2 * max
- * |f_bf16 - f_fp32| over n_points seeded uniform points of the grid's volume
- * together with the lattice points of a coarse grid around the surface.
- * Stores eps in the SDB (used when gh_options.eps < 0) and, if eps_out is
- * not NULL, writes it to the host float.  Synchronises the stream. */
+ * |f_bf16 - f_ref| over n_points seeded uniform points of the grid's volume
+ * together with the lattice points a BF16 hopping run of a grid of N/4 (at
+ * least 32) cells evaluates next to the surface, f_ref being the split-BF16
+ * evaluator (GH_BF16_REFINE_X6; FP32-level accuracy, within ~1e-8 of FP32
+ * here, far inside the factor 2).  Stores eps in the SDB (used when
+ * gh_options.eps < 0) and, if eps_out is not NULL, writes it to the host
+ * float.  Synchronises the stream.  GH_ERR_UNIMPLEMENTED when the SDB's
+ * width / depth has no BF16 path. */
 int gh_sdb_calibrate(gh_sdb *sdb, const gh_grid *grid, int64_t n_points, uint64_t seed, float *eps_out,
                      void *stream);
 

@@ -873,10 +873,12 @@ void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStre
 // face is a surface cell and is queued once (visited bit per cell).  Each
 // queued cell gets Marching Cubes at once from its own eight corner values
 // (the hopper's evaluator at the same lattice points, so the triangles are
-// bit-identical to the other methods').  Persistent warps take up to 32
-// queued cells at a time; the queue (in the marks buffer, cell id + 1 per
-// slot, 0 = not yet written) ends when no cell is queued and none is being
-// processed (q_pending == 0).  Waits are bounded (2 s of %globaltimer).
+// bit-identical to the other methods').  The queue lives in the marks buffer
+// (cell id + 1 per slot, 0 = not yet written); persistent warps take tickets
+// of 32 future slots (one atomic each), every lane polls its own slot and the
+// warp processes the cells as they are pushed; the crawl ends when no cell
+// is queued or in work (q_pending == 0).  Waits are bounded (2 s of
+// %globaltimer) and idle polling backs off.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long CONT_WAIT_NS = 2000000000ull;
 
@@ -947,90 +949,86 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
     volatile unsigned long long *vq = reinterpret_cast<volatile unsigned long long *>(s.marks_raw);
     volatile Counters *vc = s.ctr;
     unsigned long long evals = 0;
-    for (;;) {
-        // claim up to 32 queued cells (lane 0), or learn that the crawl is over
-        unsigned long long h = 0;
-        int n = 0;
-        if (lane == 0) {
-            const unsigned long long t0 = gtimer_ns();
-            unsigned nap = 32;  // an idle warp backs off, so that the few with work are not starved
-            for (unsigned it = 1;; ++it) {
-                h = vc->q_head;
-                unsigned long long t = vc->marks;
-                t = t < cap ? t : cap;
-                if (h < t) {
-                    const int want = (int)(t - h < 32ull ? t - h : 32ull);
-                    if (atomicCAS(&s.ctr->q_head, h, h + (unsigned long long)want) == h) {
-                        n = want;
-                        break;
+    bool over = false;
+    while (!over) {
+        // a ticket: the next 32 queue slots, each lane waiting for its own
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&s.ctr->q_head, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= cap) break;  // beyond the queue: nothing will come
+        const unsigned long long slot = base + lane;
+        bool done = slot >= cap;
+        unsigned long long t0 = gtimer_ns(), seen = 0;  // the wait limit runs while the queue does not grow
+        unsigned nap = 32;  // idle polling backs off
+        for (;;) {
+            const unsigned long long v = done ? 0ull : vq[slot];
+            const bool ready = v != 0ull;
+            if (__ballot_sync(FULL, ready)) {
+                const unsigned long long c = ready ? v - 1ull : 0ull;
+                const int k = (int)(c % (unsigned long long)N), j = (int)((c / N) % N);
+                const int i = (int)(c / ((unsigned long long)N * N));
+                float fv[8];
+                if (ready) {
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const float f = csg_eval(sprim, nprim, fmaf((float)(i + (b & 1)), g.h, g.lo[0]),
+                                                 fmaf((float)(j + ((b >> 1) & 1)), g.h, g.lo[1]),
+                                                 fmaf((float)(k + (b >> 2)), g.h, g.lo[2]));
+                        if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
+                        fv[b] = f;
                     }
-                    continue;
+                    evals += 8;
                 }
-                if (vc->q_pending == 0ull || (vc->flags & FLAG_TIMEOUT)) break;
-                if ((it & 15u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
+                emit_cells(g, s.ctr, out, ready, i, j, k, fv, stage[threadIdx.x >> 5], tab);
+                // the neighbours across the faces the surface crosses
+                long long pushed = 0;
+                if (ready) {
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            int neg = 0;
+#pragma unroll
+                            for (int b = 0; b < 8; ++b)
+                                if (((b >> ax) & 1) == side) neg += fv[b] < 0.f;
+                            if (neg == 0 || neg == 4) continue;
+                            int n3[3] = {i, j, k};
+                            n3[ax] += side ? 1 : -1;
+                            if (n3[ax] < 0 || n3[ax] >= N) continue;
+                            const unsigned long long nc = ((unsigned long long)n3[0] * N + n3[1]) * N + n3[2];
+                            if (visit(s.vis, nc) && enqueue(s, nc)) ++pushed;
+                        }
+                    pushed -= 1;  // this cell is finished
+                    done = true;
+                }
+                __threadfence();  // the queued slots are visible before the count says so
+                for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(FULL, pushed, o);
+                if (lane == 0 && pushed) atomicAdd(&s.ctr->q_pending, (unsigned long long)pushed);
+                if (__all_sync(FULL, done)) break;  // the ticket is used up: take the next
+                nap = 32;
+                continue;
+            }
+            // nothing arrived: the crawl is over when no cell is queued or in work
+            int fin = 0;
+            if (lane == 0) {
+                fin = vc->q_pending == 0ull || (vc->flags & FLAG_TIMEOUT) ? 1 : 0;
+                const unsigned long long tail = vc->marks;
+                if (tail != seen) {
+                    seen = tail;
+                    t0 = gtimer_ns();
+                }
+                if (!fin && gtimer_ns() - t0 > CONT_WAIT_NS) {
                     atomicOr(&s.ctr->flags, FLAG_TIMEOUT);
-                    break;
-                }
-                __nanosleep(nap);
-                nap = nap < 1024u ? 2u * nap : 1024u;
-            }
-        }
-        n = __shfl_sync(FULL, n, 0);
-        h = __shfl_sync(FULL, h, 0);
-        if (n == 0) break;
-        const bool valid = lane < n;
-        unsigned long long c = 0;
-        if (valid) {
-            // the pusher writes the slot right after reserving it
-            const unsigned long long t0 = gtimer_ns();
-            unsigned long long v;
-            for (unsigned it = 1;; ++it) {
-                v = vq[h + lane];
-                if (v) break;
-                if ((it & 63u) == 0u && gtimer_ns() - t0 > CONT_WAIT_NS) {
-                    atomicOr(&s.ctr->flags, FLAG_TIMEOUT);
-                    break;
+                    fin = 1;
                 }
             }
-            c = v ? v - 1ull : 0ull;
-        }
-        const int k = (int)(c % (unsigned long long)N), j = (int)((c / N) % N), i = (int)(c / ((unsigned long long)N * N));
-        float fv[8];
-        if (valid) {
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const float f = csg_eval(sprim, nprim, fmaf((float)(i + (b & 1)), g.h, g.lo[0]),
-                                         fmaf((float)(j + ((b >> 1) & 1)), g.h, g.lo[1]),
-                                         fmaf((float)(k + (b >> 2)), g.h, g.lo[2]));
-                if (!isfinite(f)) atomicOr(&s.ctr->flags, FLAG_NONFINITE);
-                fv[b] = f;
+            if (__shfl_sync(FULL, fin, 0)) {
+                over = true;
+                break;
             }
-            evals += 8;
+            __nanosleep(nap);
+            nap = nap < 1024u ? 2u * nap : 1024u;
         }
-        emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage[threadIdx.x >> 5], tab);
-        // the neighbours across the faces the surface crosses
-        long long pushed = 0;
-        if (valid) {
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    int neg = 0;
-#pragma unroll
-                    for (int b = 0; b < 8; ++b)
-                        if (((b >> ax) & 1) == side) neg += fv[b] < 0.f;
-                    if (neg == 0 || neg == 4) continue;
-                    int n3[3] = {i, j, k};
-                    n3[ax] += side ? 1 : -1;
-                    if (n3[ax] < 0 || n3[ax] >= N) continue;
-                    const unsigned long long nc = ((unsigned long long)n3[0] * N + n3[1]) * N + n3[2];
-                    if (visit(s.vis, nc) && enqueue(s, nc)) ++pushed;
-                }
-            pushed -= 1;  // this cell is finished
-        }
-        __threadfence();  // the queued slots are visible before the count says so
-        for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(FULL, pushed, o);
-        if (lane == 0 && pushed) atomicAdd(&s.ctr->q_pending, (unsigned long long)pushed);
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(FULL, evals, o);
     if (lane == 0 && evals) atomicAdd(&s.ctr->hop_evals, evals);
