@@ -895,7 +895,8 @@ __device__ __forceinline__ bool visit(uint32_t *vis, unsigned long long c) {
 }
 
 // Queues cell c: false when the queue is full (the overflow flag is set and
-// the cell is dropped; the caller does not count it as pending).
+// the cell is dropped).  The caller has already counted c as pending, so that
+// no worker can finish it before it is counted.
 __device__ __forceinline__ bool enqueue(const Scratch &s, unsigned long long c) {
     const unsigned long long slot = atomicAdd(&s.ctr->marks, 1ull);
     if (slot >= (unsigned long long)s.cap_marks) {
@@ -928,7 +929,11 @@ __global__ void k_cont_seed(const Prim *__restrict__ gprims, int nprim, GridP g,
         ++evals;
         if ((fp < 0.f) != (fn < 0.f)) {
             const unsigned long long c = ((unsigned long long)a * N + ijk[1]) * N + ijk[2];
-            if (visit(s.vis, c) && enqueue(s, c)) atomicAdd(&s.ctr->q_pending, 1ull);
+            if (visit(s.vis, c)) {
+                atomicAdd(&s.ctr->q_pending, 1ull);
+                __threadfence();
+                if (!enqueue(s, c)) atomicAdd(&s.ctr->q_pending, ~0ull);  // dropped: uncount it
+            }
             break;
         }
         fp = fn;
@@ -980,8 +985,10 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
                     evals += 8;
                 }
                 emit_cells(g, s.ctr, out, ready, i, j, k, fv, stage[threadIdx.x >> 5], tab);
-                // the neighbours across the faces the surface crosses
-                long long pushed = 0;
+                // the neighbours across the faces the surface crosses that this
+                // cell visits first: counted as pending, then queued
+                unsigned long long nb[6];
+                int nn = 0;
                 if (ready) {
 #pragma unroll
                     for (int ax = 0; ax < 3; ++ax)
@@ -996,14 +1003,24 @@ __global__ void __launch_bounds__(256) k_cont_csg(const Prim *__restrict__ gprim
                             n3[ax] += side ? 1 : -1;
                             if (n3[ax] < 0 || n3[ax] >= N) continue;
                             const unsigned long long nc = ((unsigned long long)n3[0] * N + n3[1]) * N + n3[2];
-                            if (visit(s.vis, nc) && enqueue(s, nc)) ++pushed;
+                            if (visit(s.vis, nc)) nb[nn++] = nc;
                         }
-                    pushed -= 1;  // this cell is finished
+                }
+                int cnt = nn;
+                for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+                if (lane == 0 && cnt) atomicAdd(&s.ctr->q_pending, (unsigned long long)cnt);
+                __syncwarp();
+                __threadfence();  // counted before any of them can be taken
+                long long fin = 0;
+                for (int q = 0; q < nn; ++q)
+                    if (!enqueue(s, nb[q])) ++fin;  // dropped (queue full): uncounted below
+                if (ready) {
+                    ++fin;  // this cell is finished
                     done = true;
                 }
-                __threadfence();  // the queued slots are visible before the count says so
-                for (int o = 16; o > 0; o >>= 1) pushed += __shfl_xor_sync(FULL, pushed, o);
-                if (lane == 0 && pushed) atomicAdd(&s.ctr->q_pending, (unsigned long long)pushed);
+                __threadfence();  // its queued cells are visible before it leaves the count
+                for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(FULL, fin, o);
+                if (lane == 0 && fin) atomicAdd(&s.ctr->q_pending, (unsigned long long)(-fin));
                 if (__all_sync(FULL, done)) break;  // the ticket is used up: take the next
                 nap = 32;
                 continue;
