@@ -34,7 +34,7 @@ using namespace tc;
 
 constexpr int EPI_T0 = 128;  // first epilogue thread (warp 4)
 constexpr int TM = 128;      // rows per tile
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 2;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLOW;
@@ -46,12 +46,12 @@ constexpr int MAXMID = 8;  // hidden layers supported by the tensor-core engine
 template <int W>
 struct SmemB {
     uint8_t a[2][W / 64][TM * 128];  // A operands: one per tile, K-blocks of 128 rows x 128 B (1024-aligned)
-    uint8_t w[NSTAGE][W * 64];       // weight ring: one half (W/2 output rows x 128 B) of a K-block per stage
+    uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
     float4 w0b[2][W];                // per tile: layer-0 rows and biases of its current item, by output
                                      // pairs (2p, 2p+1): {wx, wx', wy, wy'}, {wz, wz', b, b'}
     float bmid[2][MAXMID * W];       // per tile: hidden-layer biases
     float wout[2][W];                // per tile: output-layer weights
-    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2][2], a_full[2], item_ready[2], drain;
+    unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2], a_full[2], item_ready[2], drain;
     const uint16_t *cur_wbf[2];      // per tile: weights of its current item
     int done[2];                     // per tile: no more work
     uint32_t tmem_base;
@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                float *__restrict__ outv, unsigned long long wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int KB = W / 64;
-    constexpr uint32_t STAGE_BYTES = W * 64;  // half of a K-block: its W/2 output rows
+    constexpr uint32_t STAGE_BYTES = W * 128;
     constexpr uint32_t TMEM_COLS = TILES * W < 32 ? 32 : TILES * W;
-    constexpr uint32_t IDESC = idesc_bf16(TM, W / 2);  // one N-half of a layer per MMA
+    constexpr uint32_t IDESC = idesc_bf16(TM, W);
     SmemB<W> &sm = *reinterpret_cast<SmemB<W> *>(smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int *ctl = &sm.ctl;
@@ -124,8 +124,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             mbar_init(&sm.empty[i], 1);
         }
         for (int t = 0; t < 2; ++t) {
-            mbar_init(&sm.acc_full[t][0], 1);
-            mbar_init(&sm.acc_full[t][1], 1);
+            mbar_init(&sm.acc_full[t], 1);
             mbar_init(&sm.a_full[t], 128);
             mbar_init(&sm.item_ready[t], 1);
             sm.cur_wbf[t] = items[0].m.wbf;
@@ -171,8 +170,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     }
                     src[t] = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf[t]);
                 }
-                for (int q = 0; q < 2 * KB && go; ++q) {  // half 0's K-blocks, then half 1's
-                    const int h = q / KB, kb = q - h * KB;
+                for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(issued % NSTAGE);
                     const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
                     if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
@@ -180,8 +178,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                         break;
                     }
                     mbar_expect_tx(&sm.full[st], STAGE_BYTES);
-                    bulk_g2s(sm.w[st], src[t] + (size_t)(lt[t] * KB + kb) * (2 * STAGE_BYTES) + (size_t)h * STAGE_BYTES,
-                             STAGE_BYTES, &sm.full[st]);
+                    bulk_g2s(sm.w[st], src[t] + (size_t)(lt[t] * KB + kb) * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
                     ++issued;
                 }
                 lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
@@ -216,28 +213,23 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 }
                 tc_fence_after();
                 const uint32_t at = su32(&sm.a[t][0][0]);
-                // the layer's two N-halves one after the other: the epilogue
-                // turns half 0 into operands while the MMAs of half 1 run
-                for (int h = 0; h < 2 && go; ++h) {
-                    for (int kb = 0; kb < KB; ++kb) {
-                        const int st = (int)(consumed % NSTAGE);
-                        if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0,
-                                      wait_ns)) {
-                            go = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t wb = su32(sm.w[st]);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            umma(tmem + (uint32_t)(t * W + h * (W / 2)), sdesc(at + kb * (TM * 128) + k * 32),
-                                 sdesc(wb + k * 32), IDESC, (kb | k) != 0);
-                        umma_commit(&sm.empty[st]);
-                        ++consumed;
+                for (int kb = 0; kb < KB; ++kb) {
+                    const int st = (int)(consumed % NSTAGE);
+                    if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0, wait_ns)) {
+                        go = false;
+                        break;
                     }
-                    if (go) umma_commit(&sm.acc_full[t][h]);
+                    tc_fence_after();
+                    const uint32_t wb = su32(sm.w[st]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        umma(tmem + (uint32_t)(t * W), sdesc(at + kb * (TM * 128) + k * 32), sdesc(wb + k * 32),
+                             IDESC, (kb | k) != 0);
+                    umma_commit(&sm.empty[st]);
+                    ++consumed;
                 }
                 if (!go) break;
+                umma_commit(&sm.acc_full[t]);
                 lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
                 if (!fin[t ^ 1]) t ^= 1;
             }
@@ -266,7 +258,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         bool done = false;
         float x = 0.f, y = 0.f;
         unsigned long long evals = 0, idx = 0;
-        uint32_t pacc[2] = {0u, 0u};
+        uint32_t pacc = 0;
         float4 *w0b = sm.w0b[t];
         float *bmid = sm.bmid[t];
         float *wout = sm.wout[t];
@@ -434,90 +426,63 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 pend_mark = false;
                 pend_mask = 0;
             }
-            // 3. hidden layers, each as two N-halves of W/2 accumulator columns:
-            //    half 0 is converted while the MMAs of half 1 run and parked,
-            //    packed as BF16, in its own consumed accumulator columns; after
-            //    half 1 both go to the next layer's A operand
+            // 3. hidden layers
             float gsum = 0.f;
-            constexpr int HC = W / 64;  // 32-column chunks per half
             for (int l = 0; l < n_mid; ++l) {
+                wait_bar(&sm.acc_full[t], pacc, ctl, CTL_ABORT, ctr0, wait_ns);
+                pacc ^= 1u;
+                __syncwarp();  // tcgen05.ld below needs the whole warp converged
+                tc_fence_after();
                 const float *bl = bmid + l * W;
-                const bool last = l + 1 == n_mid;
                 uint32_t ra[32], rb[32];
+                tmem_ld32_async(taddr, ra);
+                tmem_wait_ld();
+                if (l + 1 < n_mid) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    wait_bar(&sm.acc_full[t][h], pacc[h], ctl, CTL_ABORT, ctr0, wait_ns);
-                    pacc[h] ^= 1u;
-                    __syncwarp();  // tcgen05.ld below needs the whole warp converged
-                    tc_fence_after();
-                    tmem_ld32_async(taddr + 32 * (h * HC), ra);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int jj = 0; jj < HC; ++jj) {
-                        const int j = h * HC + jj;  // chunk of columns 32j .. 32j + 31
+                    for (int j = 0; j < W / 32; ++j) {
                         // the next chunk's load runs while this one is converted
-                        uint32_t(&cu)[32] = (jj & 1) ? rb : ra;
-                        uint32_t(&nx)[32] = (jj & 1) ? ra : rb;
-                        if (jj + 1 < HC) tmem_ld32_async(taddr + 32 * (j + 1), nx);
-                        if (!last) {
-                            const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
-                            uint32_t pk[16];
+                        uint32_t(&cu)[32] = (j & 1) ? rb : ra;
+                        uint32_t(&nx)[32] = (j & 1) ? ra : rb;
+                        if (j + 1 < W / 32) tmem_ld32_async(taddr + 32 * (j + 1), nx);
+                        const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
+                        const int kb = j >> 1, c0 = (j & 1) * 4;
 #pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const float4 b0 = bp[2 * c], b1 = bp[2 * c + 1];
-                                pk[4 * c + 0] = pack_relu_bf16(__uint_as_float(cu[8 * c + 0]) + b0.x,
+                        for (int c = 0; c < 4; ++c) {
+                            const float4 b0 = bp[2 * c], b1 = bp[2 * c + 1];
+                            const uint32_t p0 = pack_relu_bf16(__uint_as_float(cu[8 * c + 0]) + b0.x,
                                                                __uint_as_float(cu[8 * c + 1]) + b0.y);
-                                pk[4 * c + 1] = pack_relu_bf16(__uint_as_float(cu[8 * c + 2]) + b0.z,
+                            const uint32_t p1 = pack_relu_bf16(__uint_as_float(cu[8 * c + 2]) + b0.z,
                                                                __uint_as_float(cu[8 * c + 3]) + b0.w);
-                                pk[4 * c + 2] = pack_relu_bf16(__uint_as_float(cu[8 * c + 4]) + b1.x,
+                            const uint32_t p2 = pack_relu_bf16(__uint_as_float(cu[8 * c + 4]) + b1.x,
                                                                __uint_as_float(cu[8 * c + 5]) + b1.y);
-                                pk[4 * c + 3] = pack_relu_bf16(__uint_as_float(cu[8 * c + 6]) + b1.z,
+                            const uint32_t p3 = pack_relu_bf16(__uint_as_float(cu[8 * c + 6]) + b1.z,
                                                                __uint_as_float(cu[8 * c + 7]) + b1.w);
-                            }
-                            if (h == 0) {
-                                // columns 16j .. 16j + 15 are consumed (chunks <= j are loaded)
-                                tmem_st16(taddr + 16 * j, pk);
-                            } else {
-                                const int kb = j >> 1, c0 = (j & 1) * 4;
-#pragma unroll
-                                for (int c = 0; c < 4; ++c)
-                                    sts128(arow + kb * (TM * 128) + (((c0 + c) ^ sw) << 4), pk[4 * c], pk[4 * c + 1],
-                                           pk[4 * c + 2], pk[4 * c + 3]);
-                            }
-                        } else {
-                            // output layer in FP32 from the accumulators, columns in order
-                            const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
-                            const float4 *wp = reinterpret_cast<const float4 *>(wout + 32 * j);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                const float4 b = bp[c], w = wp[c];
-                                gsum = fmaf(w.x, fmaxf(__uint_as_float(cu[4 * c + 0]) + b.x, 0.f), gsum);
-                                gsum = fmaf(w.y, fmaxf(__uint_as_float(cu[4 * c + 1]) + b.y, 0.f), gsum);
-                                gsum = fmaf(w.z, fmaxf(__uint_as_float(cu[4 * c + 2]) + b.z, 0.f), gsum);
-                                gsum = fmaf(w.w, fmaxf(__uint_as_float(cu[4 * c + 3]) + b.w, 0.f), gsum);
-                            }
+                            sts128(arow + kb * (TM * 128) + (((c0 + c) ^ sw) << 4), p0, p1, p2, p3);
                         }
                         tmem_wait_ld();
-                    }
-                    if (h == 0 && !last) tmem_wait_st();
-                }
-                if (!last) {
-                    // the parked half 0 into the A operand (K-blocks of the first W/2 inputs)
-#pragma unroll
-                    for (int jj = 0; jj < HC; ++jj) {
-                        uint32_t pk[16];
-                        tmem_ld16_async(taddr + 16 * jj, pk);
-                        tmem_wait_ld();
-                        const int kb = jj >> 1, c0 = (jj & 1) * 4;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            sts128(arow + kb * (TM * 128) + (((c0 + c) ^ sw) << 4), pk[4 * c], pk[4 * c + 1],
-                                   pk[4 * c + 2], pk[4 * c + 3]);
                     }
                     tc_fence_before();
                     fence_async_smem();
                     mbar_arrive(&sm.a_full[t]);
                 } else {
+                    // output layer in FP32 from the accumulators
+#pragma unroll
+                    for (int j = 0; j < W / 32; ++j) {
+                        uint32_t(&cu)[32] = (j & 1) ? rb : ra;
+                        uint32_t(&nx)[32] = (j & 1) ? ra : rb;
+                        if (j + 1 < W / 32) tmem_ld32_async(taddr + 32 * (j + 1), nx);
+                        const float4 *bp = reinterpret_cast<const float4 *>(bl + 32 * j);
+                        const float4 *wp = reinterpret_cast<const float4 *>(wout + 32 * j);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float4 b = bp[c], w = wp[c];
+                            gsum = fmaf(w.x, fmaxf(__uint_as_float(cu[4 * c + 0]) + b.x, 0.f), gsum);
+                            gsum = fmaf(w.y, fmaxf(__uint_as_float(cu[4 * c + 1]) + b.y, 0.f), gsum);
+                            gsum = fmaf(w.z, fmaxf(__uint_as_float(cu[4 * c + 2]) + b.z, 0.f), gsum);
+                            gsum = fmaf(w.w, fmaxf(__uint_as_float(cu[4 * c + 3]) + b.w, 0.f), gsum);
+                        }
+                        tmem_wait_ld();
+                    }
                     tc_fence_before();
                 }
             }

@@ -1056,6 +1056,8 @@ void launch_cont_csg(const Prim *prims, int nprim, const GridP &g, Scratch &s, c
     const size_t smem = (size_t)nprim * sizeof(Prim);
     const unsigned long long ncell = (unsigned long long)g.N * g.N * g.N;
     cudaMemsetAsync(s.vis, 0, sizeof(uint32_t) * ((ncell + 31) / 32), st);
+    // the queue's slots read 0 until written (the scratch holds earlier calls' data)
+    cudaMemsetAsync(s.marks_raw, 0, sizeof(unsigned long long) * (size_t)s.cap_marks, st);
     k_cont_seed<<<(n_seeds + 127) / 128, 128, smem, st>>>(prims, nprim, g, s, seeds, n_seeds);
     cudaFuncSetAttribute(k_cont_csg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // one CTA (8 warps) per SM: the crawl's front holds a few thousand cells
