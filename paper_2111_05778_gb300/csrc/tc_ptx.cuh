@@ -43,6 +43,20 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
     return ok != 0;
 }
 
+// As mbar_try, but a thread whose phase is not complete is suspended (it
+// issues nothing) until the phase completes or about hint_ns have passed.
+__device__ __forceinline__ bool mbar_try_sleep(unsigned long long *b, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase of the given parity.  Returns false without waiting
 // further once (ctl & give_up) is set; after limit_ns nanoseconds sets the
 // abort bit and the device error flag and returns false.  The waits of the
@@ -56,11 +70,14 @@ __device__ __noinline__ bool wait_bar(unsigned long long *b, uint32_t parity, vo
         return false;
     }
     if (mbar_try(b, parity)) return true;
+    // the waiting thread sleeps in the barrier instead of polling, so that it
+    // takes no issue slots from the threads that share its scheduler
+    const uint32_t hint = limit_ns < 20000ull ? (uint32_t)limit_ns : 20000u;
     const unsigned long long t0 = gtimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try(b, parity)) return true;
+    for (;;) {
+        if (mbar_try_sleep(b, parity, hint)) return true;
         if (*ctl & give_up) return false;
-        if (((it & 255) == 0 || limit_ns < 100000ull) && gtimer() - t0 > limit_ns) {
+        if (gtimer() - t0 > limit_ns) {
             atomicOr((int *)ctl, CTL_ABORT);
             atomicOr(&ctr->flags, FLAG_TIMEOUT);
             return false;
