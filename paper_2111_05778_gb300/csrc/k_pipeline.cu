@@ -606,20 +606,50 @@ void launch_eval_points_csg(const Prim *prims, int nprim, const float *p, long l
 // ---------------------------------------------------------------------------
 // 5. Marching Cubes on the marked cells.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t find_c(const unsigned long long *__restrict__ vkey, uint32_t lo, uint32_t hi,
-                                           uint32_t c) {
-    // vkey[lo..hi) has ascending c (upper 32 bits); c is present by construction
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if ((uint32_t)(vkey[mid] >> 32) <= c) lo = mid; else hi = mid;
+// List indices of the corners c = k of each lane's marked cell (i, j, k) on
+// its four vertical lattice lines (q = ox + 2 oy; corner c = k + 1 is the next
+// entry).  Every lane of the warp calls it; valid == false for lanes without
+// a cell.  A lane whose cell continues a run of consecutive cells of one
+// column in the lanes below takes the indices of the run's first cell plus
+// its offset: the corners of a run are consecutive entries of each line's
+// list (each list holds every corner of the run once, in ascending c).  The
+// first cells of runs search; the four lists advance together in one
+// branchless binary search, so the loads of the four lines overlap.
+__device__ __forceinline__ void cell_corners(const Scratch &s, int N, bool valid, uint32_t col, int i, int j, int k,
+                                             uint32_t (&idx)[4]) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t pcol = __shfl_up_sync(FULL, col, 1);
+    const int pk = __shfl_up_sync(FULL, k, 1);
+    const int pvalid = __shfl_up_sync(FULL, (int)valid, 1);
+    const bool cont = lane > 0 && valid && pvalid && pcol == col && pk + 1 == k;
+    const unsigned heads = __ballot_sync(FULL, valid && !cont);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) idx[q] = 0;
+    if (valid && !cont) {
+        const uint32_t N1 = (uint32_t)N + 1u;
+        const uint32_t l0 = (uint32_t)i * N1 + (uint32_t)j, l1 = l0 + N1;  // lines (i, j), (i + 1, j)
+        const uint32_t a0 = s.lineoff[l0], a1 = s.lineoff[l0 + 1], a2 = s.lineoff[l0 + 2];
+        const uint32_t b0 = s.lineoff[l1], b1 = s.lineoff[l1 + 1], b2 = s.lineoff[l1 + 2];
+        const uint32_t hi[4] = {a1, b1, a2, b2};
+        idx[0] = a0;
+        idx[1] = b0;
+        idx[2] = a1;
+        idx[3] = b1;
+        const uint32_t len = max(max(a1 - a0, b1 - b0), max(a2 - a1, b2 - b1));
+        // the largest p in [lo, hi) with c(p) <= k: c = k is in every list
+        for (uint32_t step = len > 1u ? 1u << (31 - __clz(len - 1u)) : 0u; step; step >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t p = idx[q] + step;
+                if (p < hi[q] && (uint32_t)(s.vkey[p] >> 32) <= (uint32_t)k) idx[q] = p;
+            }
+        }
     }
-    return lo;
-}
-
-// list index of corner (q, c = k) of marked cell (i, j, k), q = ox + 2 oy
-__device__ __forceinline__ uint32_t corner_index(const Scratch &s, int N1, int i, int j, int k, int q) {
-    const uint32_t line = (uint32_t)(i + (q & 1)) * N1 + (uint32_t)(j + (q >> 1));
-    return find_c(s.vkey, s.lineoff[line], s.lineoff[line + 1], (uint32_t)k);
+    const unsigned below = heads & (lane == 31 ? FULL : ((2u << lane) - 1u));
+    const int hl = below ? 31 - __clz(below) : lane;
+    const int hk = __shfl_sync(FULL, k, hl);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) idx[q] = __shfl_sync(FULL, idx[q], hl) + (uint32_t)(k - hk);
 }
 
 // The Marching Cubes table in shared memory: the lanes of a warp look up
@@ -774,17 +804,16 @@ __device__ __forceinline__ void mc_cells(const GridP &g, const Scratch &s, const
         const unsigned long long r = m < M ? s.marks_csr[m] : MARK_EMPTY;
         const bool valid = !mark_empty(r);  // cells marked empty have no triangles
         float fv[8];
-        int i = 0, j = 0, k = 0;
+        const uint32_t col = mark_col(r);
+        const int k = (int)mark_k(r);
+        const int i = (int)(col / (uint32_t)N), j = (int)(col - (uint32_t)i * N);
+        uint32_t idx[4];
+        cell_corners(s, N, valid, col, i, j, k, idx);
         if (valid) {
-            const uint32_t col = mark_col(r);
-            k = (int)mark_k(r);
-            i = (int)(col / (uint32_t)N);
-            j = (int)(col - (uint32_t)i * N);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t idx = corner_index(s, N + 1, i, j, k, q);
-                fv[q] = s.vval[idx];
-                fv[q + 4] = s.vval[idx + 1];
+                fv[q] = s.vval[idx[q]];
+                fv[q + 4] = s.vval[idx[q] + 1];
             }
         }
         emit_cells(g, s.ctr, out, valid, i, j, k, fv, stage, tab, bs);
@@ -1089,16 +1118,22 @@ __device__ __forceinline__ void refine_select(const GridP &g, const Scratch &s, 
     // the 12 cube edges as corner pairs (corner b at (b&1, b>>1&1, b>>2&1))
     const uint8_t ea[12] = {0, 2, 4, 6, 0, 1, 4, 5, 0, 1, 2, 3};
     const uint8_t eb[12] = {1, 3, 5, 7, 2, 3, 6, 7, 4, 5, 6, 7};
-    for (unsigned long long m = t0; m < M; m += stride) {
-        const unsigned long long r = s.marks_csr[m];
-        if (mark_empty(r)) continue;  // no corners evaluated, no crossing edge
-        const uint32_t col = mark_col(r), k = mark_k(r);
+    // warp-uniform loop (t0 - lane starts the warp's marks; stride is a
+    // multiple of 32) so that the warp shares its corner searches
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long mb = t0 - (unsigned long long)lane; mb < M; mb += stride) {
+        const unsigned long long m = mb + (unsigned long long)lane;
+        const unsigned long long r = m < M ? s.marks_csr[m] : MARK_EMPTY;
+        const bool valid = !mark_empty(r);  // cells marked empty: no corners evaluated, no crossing edge
+        const uint32_t col = mark_col(r);
+        const int k = (int)mark_k(r);
         const int i = (int)(col / (uint32_t)g.N), j = (int)(col - (uint32_t)i * g.N);
         uint32_t vi[8];
         float fv[8];
+        cell_corners(s, g.N, valid, col, i, j, k, *reinterpret_cast<uint32_t(*)[4]>(vi));
+        if (!valid) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            vi[q] = corner_index(s, g.N + 1, i, j, (int)k, q);
             vi[q + 4] = vi[q] + 1;
             fv[q] = s.vval[vi[q]];
             fv[q + 4] = s.vval[vi[q] + 1];
