@@ -510,11 +510,19 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
 def _src_hash(rel):
+    """First 16 hex digits of the SHA-256 of a source file, or of the
+    concatenation of a list of them (a kernel's file and the headers it
+    inlines)."""
     import hashlib
 
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for r in [rel] if isinstance(rel, str) else rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel, units):
