@@ -668,9 +668,12 @@ __device__ __forceinline__ void load_tab(McTab &t) {
     __syncthreads();
 }
 
-// Triangles a warp stages in shared memory before writing them out: at most
-// 5 per cell, 32 cells, 9 floats each.
-constexpr int EMIT_STAGE = 32 * 5 * 9;
+// Triangles a warp stages in shared memory before writing them out: room for
+// two per cell on average (32 cells, 9 floats each); a warp whose cells have
+// more (up to 5 per cell) writes them directly.  The small buffer leaves room
+// for more resident warps, which hide this latency-bound kernel's loads.
+constexpr int EMIT_TRIS = 32 * 2;
+constexpr int EMIT_STAGE = EMIT_TRIS * 9;
 
 // Case index, triangle table and warp prefix-sum emit of one cell per lane;
 // every lane of the warp calls it (valid == false for lanes without a cell).
@@ -751,8 +754,13 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
         }
     }
     if (!wtot) return;
+    const unsigned long long cap = (unsigned long long)out.capacity_tris;
+    const bool staged = wtot <= EMIT_TRIS;  // warp-uniform
     for (int t = 0; t < nt; ++t) {
-        float *pos = stage + 9 * (loc + t);
+        const unsigned long long ti = wbase + (unsigned long long)(loc + t);
+        // staged: this triangle's slot in the warp's buffer; otherwise its
+        // place in the output (nothing is written beyond the capacity)
+        float *pos = staged ? stage + 9 * (loc + t) : (ti < cap ? out.tri_xyz + 9 * ti : nullptr);
         unsigned long long key[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -769,23 +777,24 @@ __device__ __forceinline__ void emit_cells(const GridP &g, Counters *ctr, const 
             if (ax == 0) px = fmaf(tt, g.h, px);
             else if (ax == 1) py = fmaf(tt, g.h, py);
             else pz = fmaf(tt, g.h, pz);
-            pos[3 * v] = px;
-            pos[3 * v + 1] = py;
-            pos[3 * v + 2] = pz;
+            if (pos) {
+                pos[3 * v] = px;
+                pos[3 * v + 1] = py;
+                pos[3 * v + 2] = pz;
+            }
             key[v] = (unsigned long long)ax * N13 + (unsigned long long)la +
                      (unsigned long long)N1 * ((unsigned long long)lb + (unsigned long long)N1 * lc);
         }
-        const unsigned long long ti = wbase + (unsigned long long)(loc + t);
-        if (out.tri_keys && ti < (unsigned long long)out.capacity_tris) {
+        if (out.tri_keys && ti < cap) {
             unsigned long long *kd = reinterpret_cast<unsigned long long *>(out.tri_keys) + ti * 3;
             kd[0] = key[0];
             kd[1] = key[1];
             kd[2] = key[2];
         }
     }
+    if (!staged) return;
     __syncwarp();
     // the warp's range [wbase, wbase + wtot) of triangles, float by float
-    const unsigned long long cap = (unsigned long long)out.capacity_tris;
     const unsigned long long nf = wbase >= cap ? 0ull : 9ull * ((wbase + wtot > cap ? cap : wbase + wtot) - wbase);
     float *dst = out.tri_xyz + 9 * wbase;
     for (unsigned long long f = lane; f < nf; f += 32) dst[f] = stage[f];
@@ -891,8 +900,19 @@ void launch_mc_dense(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cu
     k_mc_dense<<<nsm * 16, 256, 0, st>>>(g, s, out);
 }
 
+// Blocks of 256 threads of `kernel` resident per SM (at least 1): the
+// Marching Cubes launches are one wave, each block walking the marks with a
+// grid stride.
+template <typename K>
+static int resident_per_sm(K kernel) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    return per_sm < 1 ? 1 : per_sm;
+}
+
 void launch_mc(const GridP &g, Scratch &s, const gh_mesh &out, int nsm, cudaStream_t st) {
-    k_mc<<<nsm * 8, 256, 0, st>>>(g, s, out);
+    static const int per_sm = resident_per_sm(k_mc);
+    k_mc<<<nsm * per_sm, 256, 0, st>>>(g, s, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1422,7 +1442,10 @@ __global__ void __launch_bounds__(256) k_mc_b(const Item *__restrict__ items, in
     }
 }
 
-void launch_mc_b(const Item *items, int n, int nsm, cudaStream_t st) { k_mc_b<<<nsm * 8, 256, 0, st>>>(items, n); }
+void launch_mc_b(const Item *items, int n, int nsm, cudaStream_t st) {
+    static const int per_sm = resident_per_sm(k_mc_b);
+    k_mc_b<<<nsm * per_sm, 256, 0, st>>>(items, n);
+}
 
 __global__ void k_finalize_b(const Item *__restrict__ items, int n) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
