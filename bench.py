@@ -779,8 +779,17 @@ def work_c3(args, flush, stream):
     peaks, peak_kind = measured_peaks()
     tensor_flop = sum((st["hop_evals"] + st["unique_vertices"]) * mlp_flop(W)
                       for (kind, _, _, W), st in zip(items, stats) if kind == "mlp") if precision != "fp32" else 0
-    fp32_flop = sum(st["refined_vertices"] * mlp_flop(W) for (kind, _, _, W), st in zip(items, stats)
-                    if kind == "mlp")
+    refine_flop = sum(st["refined_vertices"] * mlp_flop(W) for (kind, _, _, W), st in zip(items, stats)
+                      if kind == "mlp")
+    if precision == "bf16x6":
+        tensor_flop += 6 * refine_flop  # six BF16 products per split-BF16 evaluation
+        note = ("BF16 tensor FLOP executed by the neural items (hop and vertex evaluations, and six BF16 products "
+                "per split-BF16 refinement) over the whole batch time (analytic items, lists and Marching Cubes "
+                "included in the time)")
+    else:
+        note = ("BF16 tensor FLOP of the neural items (hop + vertex evaluations) over the whole batch time "
+                "(analytic items, FP32 refinement (%.2f TFLOP), lists and Marching Cubes included in the time)"
+                % (refine_flop / 1e12))
     bf16_peak = float(peaks.get("bf16_tflops", 1917.8))
     ach = tensor_flop / (ms / 1e3) / 1e12
     rec = {"workload": BATCH_WORKLOAD, "ms_per_batch": ms, "ms_per_mesh": ms / len(sdbs),
@@ -789,10 +798,7 @@ def work_c3(args, flush, stream):
            "triangles": sum(st["triangles"] for st in stats), "ray_block": rb, "mlp_tiles": mt,
            "autotune_ms": timings, "setup_s": setup_s,
            "roofline": {"kernel": "whole batch (graph replay)", "bound": "tensor", "achieved": ach, "peak": bf16_peak,
-                        "unit": "TFLOP/s", "frac": ach / bf16_peak, "traffic": None,
-                        "note": "BF16 tensor FLOP of the neural items (hop + vertex evaluations) over the whole "
-                                "batch time (analytic items, FP32 refinement (%.2f TFLOP), lists and Marching "
-                                "Cubes included in the time)" % (fp32_flop / 1e12),
+                        "unit": "TFLOP/s", "frac": ach / bf16_peak, "traffic": None, "note": note,
                         "peak_source": "bf16_tflops (%s)" % peak_kind},
            "clocks": clk}
     chk = gh.polygonize_batch(sdbs, Ns, precision=precision, keys=True, cells=True, ray_block=rb, mlp_tiles=mt)
