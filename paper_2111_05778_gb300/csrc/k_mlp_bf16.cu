@@ -193,45 +193,63 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         __syncwarp();
     } else if (warp == 1) {
         // ---- MMA issuer: alternates between the tiles that still have work -----
+        // The issuing thread is on the critical path (one tcgen05.mma takes
+        // about 100 cycles to issue, a K = 16 op with N = 256 runs 128), so its
+        // loop is kept lean: descriptors are built once and advanced by fixed
+        // steps (K-blocks of A and ring stages are a fixed number of 16-byte
+        // units apart, K = 16 is 2 units), a stage that has landed is taken
+        // without a call, and the per-tile state lives in scalars.
         if (lane == 0) {
             long long consumed = 0;
-            int t = 0, lt[2] = {0, 0};
-            bool fin[2] = {false, TILES < 2};
-            uint32_t pa[2] = {0u, 0u};
+            int t = 0, lt0 = 0, lt1 = 0;
+            bool fin0 = false, fin1 = TILES < 2;
+            uint32_t pa0 = 0u, pa1 = 0u;
+            constexpr unsigned long long A_KB = (TM * 128) >> 4, W_ST = STAGE_BYTES >> 4;
+            const unsigned long long ad0 = sdesc(su32(&sm.a[0][0][0])), ad1 = sdesc(su32(&sm.a[1][0][0]));
+            const unsigned long long wd0 = sdesc(su32(sm.w[0]));
             bool go = true;
-            while (go && !(fin[0] && fin[1])) {
-                if (fin[t]) {
+            while (go && !(fin0 && fin1)) {
+                if (t ? fin1 : fin0) {
                     t ^= 1;
                     continue;
                 }
-                if (!wait_bar(&sm.a_full[t], pa[t], ctl, CTL_ABORT, ctr0, wait_ns)) break;
-                pa[t] ^= 1u;
-                if (lt[t] == 0 && vdone[t]) {
-                    fin[t] = true;
-                    if (!fin[t ^ 1]) t ^= 1;
+                const uint32_t pa = t ? pa1 : pa0;
+                if (!mbar_try(&sm.a_full[t], pa) && !wait_bar(&sm.a_full[t], pa, ctl, CTL_ABORT, ctr0, wait_ns)) break;
+                if (t) pa1 ^= 1u;
+                else pa0 ^= 1u;
+                const int L = t ? lt1 : lt0;
+                if (L == 0 && vdone[t]) {
+                    if (t) fin1 = true;
+                    else fin0 = true;
+                    if (!(t ? fin0 : fin1)) t ^= 1;
                     continue;
                 }
                 tc_fence_after();
-                const uint32_t at = su32(&sm.a[t][0][0]);
+                const unsigned long long ad = t ? ad1 : ad0;
+                const uint32_t d = tmem + (uint32_t)(t * W);
                 for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(consumed % NSTAGE);
-                    if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NSTAGE) & 1), ctl, CTL_ABORT, ctr0, wait_ns)) {
+                    const uint32_t par = (uint32_t)((consumed / NSTAGE) & 1);
+                    if (!mbar_try(&sm.full[st], par) &&
+                        !wait_bar(&sm.full[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
                         go = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t wb = su32(sm.w[st]);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        umma(tmem + (uint32_t)(t * W), sdesc(at + kb * (TM * 128) + k * 32), sdesc(wb + k * 32),
-                             IDESC, (kb | k) != 0);
+                    const unsigned long long a = ad + (unsigned long long)kb * A_KB;
+                    const unsigned long long b = wd0 + (unsigned long long)st * W_ST;
+                    umma(d, a, b, IDESC, kb != 0);
+                    umma(d, a + 2, b + 2, IDESC, 1u);
+                    umma(d, a + 4, b + 4, IDESC, 1u);
+                    umma(d, a + 6, b + 6, IDESC, 1u);
                     umma_commit(&sm.empty[st]);
                     ++consumed;
                 }
                 if (!go) break;
                 umma_commit(&sm.acc_full[t]);
-                lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
-                if (!fin[t ^ 1]) t ^= 1;
+                const int nl = L + 1 == n_mid ? 0 : L + 1;
+                if (t) lt1 = nl;
+                else lt0 = nl;
+                if (!(t ? fin0 : fin1)) t ^= 1;
             }
             // every MMA issued above has completed before TMEM is released
             umma_commit(&sm.drain);

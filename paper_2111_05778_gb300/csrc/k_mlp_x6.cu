@@ -172,11 +172,14 @@ __global__ void __launch_bounds__(384, 1)
         __syncwarp();
     } else if (warp == 1) {
         // ---- MMA issuer ---------------------------------------------------------
+        // (lean issue loop: descriptors built once and advanced by fixed steps,
+        // a stage that has landed taken without a call; k_mlp_bf16.cu)
         if (lane == 0) {
             long long consumed = 0;
             uint32_t pa = 0;
             bool go = true;
-            const uint32_t ah0 = su32(&sm.ah[0][0]);
+            constexpr unsigned long long A_KB = (TM * 128) >> 4, W_ST = STAGE_BYTES >> 4;
+            const unsigned long long ahd = sdesc(su32(&sm.ah[0][0])), wd0 = sdesc(su32(sm.w[0]));
             while (go) {
                 for (int l = 0; l < n_mid && go; ++l) {
                     if (!wait_bar(&sm.a_full, pa, ctl, CTL_ABORT, ctr0, wait_ns)) {
@@ -192,19 +195,21 @@ __global__ void __launch_bounds__(384, 1)
                     for (int part = 0; part < 3 && go; ++part) {  // weight parts low, middle, high
                         for (int kb = 0; kb < KB; ++kb) {
                             const int st = (int)(consumed % NST);
-                            if (!wait_bar(&sm.full[st], (uint32_t)((consumed / NST) & 1), ctl, CTL_ABORT, ctr0, wait_ns)) {
+                            const uint32_t par = (uint32_t)((consumed / NST) & 1);
+                            if (!mbar_try(&sm.full[st], par) &&
+                                !wait_bar(&sm.full[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
                                 go = false;
                                 break;
                             }
-                            tc_fence_after();
-                            const uint32_t wb = su32(sm.w[st]);
+                            const unsigned long long b0 = wd0 + (unsigned long long)st * W_ST;
+                            const unsigned long long a0 = ahd + (unsigned long long)kb * A_KB;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                const unsigned long long bd = sdesc(wb + k * 32);
+                                const unsigned long long bd = b0 + (unsigned long long)(2 * k);
                                 const uint32_t acol = (uint32_t)(kb * 32 + k * 8);
                                 if (part == 2) umma_ta(tmem, tmem + AL + acol, bd, IDESC, 1u);  // x_l w_h
                                 if (part >= 1) umma_ta(tmem, tmem + AM + acol, bd, IDESC, 1u);  // x_m w_m, x_m w_h
-                                umma(tmem, sdesc(ah0 + kb * (TM * 128) + k * 32), bd, IDESC,
+                                umma(tmem, a0 + (unsigned long long)(2 * k), bd, IDESC,
                                      (part | kb | k) != 0);  // x_h w_l (the layer's first op), x_h w_m, x_h w_h
                             }
                             umma_commit(&sm.empty[st]);
