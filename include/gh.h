@@ -135,6 +135,9 @@ typedef struct {
  * its error against exact arithmetic is of FP32's size, not bit-identical to
  * GH_FP32.  gh_eval takes it too (points evaluated that way). */
 #define GH_BF16_REFINE_X6 2
+/* The BF16 modes support widths 64, 128 and 256 with at most 8 hidden layers
+ * (n_mid), 7 at width 256, and the split-BF16 evaluator at most 8; other
+ * networks get GH_ERR_UNIMPLEMENTED for them (GH_FP32 takes any depth). */
 #define GH_TAU_DIAGONAL 0      /* tau = sqrt(3) h: one cell diagonal (default) */
 #define GH_TAU_HALF_DIAGONAL 1 /* tau = sqrt(3) h / 2: the tightest safe value */
 

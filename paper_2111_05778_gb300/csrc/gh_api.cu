@@ -724,8 +724,9 @@ extern "C" int gh_polygonize(const gh_grid *grid, const gh_sdb *csdb, const gh_o
         if (s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "the BF16 precisions apply to neural SDBs only");
         if (!bf16_supported(s->mlp.width))
             return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path not available for width %d", s->mlp.width);
-        if (s->mlp.n_mid > bf16_max_mid())
-            return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path supports at most %d hidden layers", bf16_max_mid());
+        if (s->mlp.n_mid > bf16_max_mid(s->mlp.width))
+            return fail(GH_ERR_UNIMPLEMENTED, "BF16 tensor-core path supports at most %d hidden layers at this width",
+                        bf16_max_mid(s->mlp.width));
         const float eps = o.eps >= 0.f ? o.eps : s->eps;
         if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "BF16 path needs eps: pass opts.eps or call gh_sdb_calibrate");
         g.eps = eps;
@@ -857,7 +858,7 @@ extern "C" int gh_eval(const gh_sdb *s, const float *p, int64_t n, float *out, i
     } else if (precision == GH_FP32) {
         launch_eval_points_mlp_fp32(s->mlp, p, n, out, nsm, st);
     } else if (precision == GH_BF16_REFINE) {
-        if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid())
+        if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid(s->mlp.width))
             return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width / depth");
         launch_eval_points_mlp_bf16(s->mlp, p, n, out, nsm, st);
     } else if (precision == GH_BF16_REFINE_X6) {
@@ -888,7 +889,7 @@ extern "C" int gh_sdb_calibrate(gh_sdb *s, const gh_grid *grid, int64_t n_points
                                 void *stream) {
     if (!s || s->kind != GH_SDB_MLP) return fail(GH_ERR_ARG, "gh_sdb_calibrate needs a neural SDB");
     if (n_points < 0 || n_points > (1ll << 26)) return fail(GH_ERR_ARG, "n_points outside [0, 2^26]");
-    if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid() || s->mlp.n_mid > x6_max_mid())
+    if (!bf16_supported(s->mlp.width) || s->mlp.n_mid > bf16_max_mid(s->mlp.width) || s->mlp.n_mid > x6_max_mid())
         return fail(GH_ERR_UNIMPLEMENTED, "no BF16 path for this width / depth");
     GridP g;
     int rc = check_grid(grid, &g, GH_TAU_DIAGONAL);
@@ -1066,9 +1067,9 @@ extern "C" int gh_polygonize_batch(int B, const gh_grid *grids, const gh_sdb *co
         if ((rc = check_grid(&grids[b], &P.g[b], o.tau_mode))) return rc;
         if ((rc = check_mesh(&outs[b]))) return rc;
         if (sd[b]->kind == GH_SDB_MLP && o.precision != GH_FP32) {
-            if (sd[b]->mlp.n_mid > bf16_max_mid())
+            if (sd[b]->mlp.n_mid > bf16_max_mid(sd[b]->mlp.width))
                 return fail(GH_ERR_UNIMPLEMENTED, "item %d: BF16 path supports at most %d hidden layers", b,
-                            bf16_max_mid());
+                            bf16_max_mid(sd[b]->mlp.width));
             const float eps = o.eps >= 0.f ? o.eps : sd[b]->eps;
             if (!(eps >= 0.f)) return fail(GH_ERR_ARG, "item %d: BF16 needs eps (calibrate the SDB)", b);
             P.g[b].eps = eps;

@@ -248,7 +248,7 @@ void launch_lattice_mlp_fp32(const Item *items, int width, int nsm, cudaStream_t
 
 // neural SDB, BF16 on tcgen05 tensor cores (k_mlp_bf16.cu)
 bool bf16_supported(int width);
-int bf16_max_mid();
+int bf16_max_mid(int width);  // hidden layers the BF16 engine supports at this width
 void launch_hop_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st);
 void launch_eval_vertices_mlp_bf16(const Item *items, int n_items, int width, int nsm, int tiles, cudaStream_t st);
 void launch_eval_points_mlp_bf16(const MlpDev &m, const float *p, long long n, float *out, int nsm,

@@ -2,8 +2,15 @@
 //
 // f(p) = (|p| - r0 + alpha g(p)) / beta / lambda, g a ReLU MLP (the neural
 // SDB of Sec. 5.2).  The W x W hidden layers run as tcgen05.mma GEMMs with
-// BF16 operands and FP32 accumulation in tensor memory; layer 0 (3 -> W) and
-// the output layer (W -> 1) run on CUDA cores in FP32.
+// BF16 operands and FP32 accumulation in tensor memory.  Layer 0 (3 -> W) is
+// one K = 16 op per tile: the point's coordinates and the layer-0 weights
+// split into BF16 high and low parts (x = x_h + x_l to 2^-17),
+// A0 = [x_h x_l x_h  y_h y_l y_h  z_h z_l z_h  1 1  0 ...] against
+// B0 = [wx_h wx_h wx_l  wy_h wy_h wy_l  wz_h wz_h wz_l  b_h b_l  0 ...], so that
+// x_h wx_h + x_l wx_h + x_h wx_l and the bias are summed in FP32 (the omitted
+// x_l wx_l is below 2^-16 of the term); its ReLU output is rounded to BF16 like
+// every hidden activation.  The output layer (W -> 1) runs on CUDA cores in
+// FP32.
 //
 // One persistent CTA per SM, 384 threads:
 //   warp 0       TMA producer: 1-D bulk copies (cp.async.bulk) of BF16 weight
@@ -41,15 +48,22 @@ constexpr unsigned long long STOP_FLAGS = FLAG_MARK_OVERFLOW | FLAG_VERT_OVERFLO
 
 enum { MODE_HOP = 0, MODE_VERTS = 1, MODE_POINTS = 2 };
 
-constexpr int MAXMID = 8;  // hidden layers supported by the tensor-core engine
+// hidden layers supported by the tensor-core engine (at width 256 one fewer,
+// for shared memory)
+template <int W>
+constexpr int maxmid_of() {
+    return W == 256 ? 7 : 8;
+}
 
 template <int W>
 struct SmemB {
     uint8_t a[2][W / 64][TM * 128];  // A operands: one per tile, K-blocks of 128 rows x 128 B (1024-aligned)
     uint8_t w[NSTAGE][W * 128];      // weight ring: one K-block of W rows x 128 B per stage
-    float4 w0b[2][W];                // per tile: layer-0 rows and biases of its current item, by output
-                                     // pairs (2p, 2p+1): {wx, wx', wy, wy'}, {wz, wz', b, b'}
-    float bmid[2][MAXMID * W];       // per tile: hidden-layer biases
+    uint8_t b0[2][W * 32];           // per tile: layer-0 operand B0 of its current item, W rows x 16 inputs
+                                     // (32-byte swizzle: row n, 16-byte chunk c at (n/8)*256 + (n%8)*32 +
+                                     // ((c ^ (n/4)%2) * 16))
+    float bmid[2][maxmid_of<W>() * W];  // per tile: hidden-layer biases
+    float zb[W];                        // zeros: the layer-0 phase adds no bias (B0 holds it)
     float wout[2][W];                // per tile: output-layer weights
     unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2], a_full[2], item_ready[2], drain;
     const uint16_t *cur_wbf[2];      // per tile: weights of its current item
@@ -77,6 +91,42 @@ __device__ __forceinline__ float outer_f(const MlpDev &m, float x, float y, floa
     return (fmaf(m.alpha, g, m.radial * r - m.r0) / m.beta) * m.inv_lam;
 }
 
+// BF16 bits (round to nearest even) of x, and of the remainder x - bf16(x)
+__device__ __forceinline__ void split2(float x, uint32_t &h, uint32_t &l) {
+    uint32_t p;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(0.f), "f"(x));
+    h = p & 0xFFFFu;
+    const float r = x - __uint_as_float(h << 16);  // exact
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(0.f), "f"(r));
+    l = p & 0xFFFFu;
+}
+
+// Row o of tile t's layer-0 operand B0 (two 16-byte chunks, inputs 0..15).
+template <int W>
+__device__ __forceinline__ void put_b0(SmemB<W> &sm, int t, int o, float wx, float wy, float wz, float b) {
+    uint32_t xh, xl, yh, yl, zh, zl, bh, bl;
+    split2(wx, xh, xl);
+    split2(wy, yh, yl);
+    split2(wz, zh, zl);
+    split2(b, bh, bl);
+    const uint32_t base = su32(sm.b0[t]) + (uint32_t)((o >> 3) * 256 + (o & 7) * 32);
+    const uint32_t sw = (uint32_t)((o >> 2) & 1);
+    sts128(base + (sw << 4), xh | (xh << 16), xl | (yh << 16), yh | (yl << 16), zh | (zh << 16));
+    sts128(base + ((1u ^ sw) << 4), zl | (bh << 16), bl, 0u, 0u);
+}
+
+// Item parameters of tile t (its 128 epilogue threads, or all threads at
+// set-up with e and the stride given): B0, hidden biases, output weights.
+template <int W>
+__device__ __forceinline__ void load_item(SmemB<W> &sm, int t, const MlpDev &mm, int e, int stride) {
+    for (int o = e; o < W; o += stride) {
+        put_b0<W>(sm, t, o, mm.w0[3 * o], mm.w0[3 * o + 1], mm.w0[3 * o + 2], mm.b0[o]);
+        sm.wout[t][o] = mm.wout[o];
+    }
+    for (int i = e; i < mm.n_mid * W; i += stride) sm.bmid[t][i] = mm.bm[i];
+    fence_async_smem();  // B0 is read by the tensor core
+}
+
 // ---------------------------------------------------------------------------
 // TILES 128-row tiles per CTA.  With two tiles the tensor core alternates
 // between them (ping-pong): while tile 0's epilogue warps turn layer l into
@@ -102,22 +152,8 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
     const int n_mid = items[0].m.n_mid;
 
     // ---- set-up ----------------------------------------------------------
-    {
-        const MlpDev &m0 = items[0].m;
-        for (int i = tid; i < TILES * W; i += blockDim.x) {
-            const int t = i / W, o = i - t * W;
-            float *q = reinterpret_cast<float *>(&sm.w0b[t][o & ~1]) + (o & 1);
-            q[0] = m0.w0[3 * o];
-            q[2] = m0.w0[3 * o + 1];
-            q[4] = m0.w0[3 * o + 2];
-            q[6] = m0.b0[o];
-            sm.wout[t][o] = m0.wout[o];
-        }
-        for (int i = tid; i < TILES * n_mid * W; i += blockDim.x) {
-            const int t = i / (n_mid * W), r = i - t * (n_mid * W);
-            sm.bmid[t][r] = m0.bm[r];
-        }
-    }
+    for (int t = 0; t < TILES; ++t) load_item<W>(sm, t, items[0].m, tid, blockDim.x);
+    for (int i = tid; i < W; i += blockDim.x) sm.zb[i] = 0.f;
     if (tid == 0) {
         for (int i = 0; i < NSTAGE; ++i) {
             mbar_init(&sm.full[i], 1);
@@ -169,6 +205,10 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                         continue;
                     }
                     src[t] = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf[t]);
+                    // the layer-0 phase streams no weights
+                    lt[t] = 1;
+                    if (!fin[t ^ 1]) t ^= 1;
+                    continue;
                 }
                 for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(issued % NSTAGE);
@@ -178,10 +218,11 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                         break;
                     }
                     mbar_expect_tx(&sm.full[st], STAGE_BYTES);
-                    bulk_g2s(sm.w[st], src[t] + (size_t)(lt[t] * KB + kb) * STAGE_BYTES, STAGE_BYTES, &sm.full[st]);
+                    bulk_g2s(sm.w[st], src[t] + (size_t)((lt[t] - 1) * KB + kb) * STAGE_BYTES, STAGE_BYTES,
+                             &sm.full[st]);
                     ++issued;
                 }
-                lt[t] = lt[t] + 1 == n_mid ? 0 : lt[t] + 1;
+                lt[t] = lt[t] == n_mid ? 0 : lt[t] + 1;  // phases 0 (layer 0) .. n_mid (hidden layers)
                 if (!fin[t ^ 1]) t ^= 1;
             }
             // the copies still in flight land before the CTA may exit
@@ -207,6 +248,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             constexpr unsigned long long A_KB = (TM * 128) >> 4, W_ST = STAGE_BYTES >> 4;
             const unsigned long long ad0 = sdesc(su32(&sm.a[0][0][0])), ad1 = sdesc(su32(&sm.a[1][0][0]));
             const unsigned long long wd0 = sdesc(su32(sm.w[0]));
+            const unsigned long long bd0 = sdesc32(su32(sm.b0[0])), bd1 = sdesc32(su32(sm.b0[1]));
             bool go = true;
             while (go && !(fin0 && fin1)) {
                 if (t ? fin1 : fin0) {
@@ -227,6 +269,10 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 tc_fence_after();
                 const unsigned long long ad = t ? ad1 : ad0;
                 const uint32_t d = tmem + (uint32_t)(t * W);
+                if (L == 0) {
+                    // layer 0: A0 in the first 16 inputs of the A operand's K-block 0
+                    umma(d, ad, t ? bd1 : bd0, IDESC, 0u);
+                } else {
                 for (int kb = 0; kb < KB; ++kb) {
                     const int st = (int)(consumed % NSTAGE);
                     const uint32_t par = (uint32_t)((consumed / NSTAGE) & 1);
@@ -244,9 +290,10 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     umma_commit(&sm.empty[st]);
                     ++consumed;
                 }
+                }
                 if (!go) break;
                 umma_commit(&sm.acc_full[t]);
-                const int nl = L + 1 == n_mid ? 0 : L + 1;
+                const int nl = L == n_mid ? 0 : L + 1;  // phases 0 (layer 0) .. n_mid (hidden layers)
                 if (t) lt1 = nl;
                 else lt0 = nl;
                 if (!(t ? fin0 : fin1)) t ^= 1;
@@ -277,7 +324,6 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
         float x = 0.f, y = 0.f;
         unsigned long long evals = 0, idx = 0;
         uint32_t pacc = 0;
-        float4 *w0b = sm.w0b[t];
         float *bmid = sm.bmid[t];
         float *wout = sm.wout[t];
         // a mark found in the previous step, written once its slot is known
@@ -391,18 +437,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 cap_marks = (unsigned long long)it->s.cap_marks;
                 col = NONE;
                 done = false;
-                {
-                    const MlpDev &mm = it->m;
-                    for (int o = row; o < W; o += 128) {
-                        float *q = reinterpret_cast<float *>(&w0b[o & ~1]) + (o & 1);
-                        q[0] = mm.w0[3 * o];
-                        q[2] = mm.w0[3 * o + 1];
-                        q[4] = mm.w0[3 * o + 2];
-                        q[6] = mm.b0[o];
-                        wout[o] = mm.wout[o];
-                    }
-                    for (int i = row; i < n_mid * W; i += 128) bmid[i] = mm.bm[i];
-                }
+                load_item<W>(sm, t, it->m, row, 128);
                 epi_any(bar, false);  // the new item's parameters are in place
                 continue;
             }
@@ -412,29 +447,21 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 if (MODE == MODE_HOP) atomicAdd(&ctr->row_slots, 128ull);
             }
             const MlpDev &m = it->m;
-            // 2. layer 0 (FP32) -> A operand (two 8-output groups per iteration
-            // so that the loads of one overlap the FMAs of the other)
-            const unsigned long long ppx = pack2(px, px), ppy = pack2(py, py), ppz = pack2(pz, pz);
-#pragma unroll 2
-            for (int o = 0; o < W; o += 8) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    // outputs o + 2e and o + 2e + 1 as one packed pair: the same
-                    // fused multiply-adds, in the same order, as the scalar form
-                    const float4 wa = w0b[o + 2 * e], wb = w0b[o + 2 * e + 1];
-                    const unsigned long long z = ffma2(pack2(wa.x, wa.y), ppx,
-                                                       ffma2(pack2(wa.z, wa.w), ppy,
-                                                             ffma2(pack2(wb.x, wb.y), ppz, pack2(wb.z, wb.w))));
-                    pk[e] = pack_relu_bf16(lo2(z), hi2(z));
-                }
-                const int kb = o >> 6, c = (o & 63) >> 3;
-                sts128(arow + kb * (TM * 128) + ((c ^ sw) << 4), pk[0], pk[1], pk[2], pk[3]);
+            // 2. the layer-0 operand A0 (BF16 high and low parts of the point, two
+            // unit inputs for the bias) in the first 16 inputs of K-block 0
+            {
+                uint32_t xh, xl, yh, yl, zh, zl;
+                split2(px, xh, xl);
+                split2(py, yh, yl);
+                split2(pz, zh, zl);
+                constexpr uint32_t ONE = 0x3F80u;  // 1.0 in BF16
+                sts128(arow + ((0 ^ sw) << 4), xh | (xl << 16), xh | (yh << 16), yl | (yh << 16), zh | (zl << 16));
+                sts128(arow + ((1 ^ sw) << 4), zh | (ONE << 16), ONE, 0u, 0u);
             }
             fence_async_smem();
             mbar_arrive(&sm.a_full[t]);
             if (MODE == MODE_HOP && pend_mark) {
-                // the previous step's marks: their slots came back during layer 0
+                // the previous step's marks: their slots came back meanwhile
                 const unsigned long long b0 = __shfl_sync(FULL, pend_base, __ffs(pend_mask) - 1);
                 if (pend_mask & (1u << lane)) {
                     const unsigned long long mi = b0 + __popc(pend_mask & lt);
@@ -444,18 +471,18 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                 pend_mark = false;
                 pend_mask = 0;
             }
-            // 3. hidden layers
+            // 3. phases 0 (layer 0, its bias in B0) .. n_mid (hidden layers)
             float gsum = 0.f;
-            for (int l = 0; l < n_mid; ++l) {
+            for (int l = 0; l <= n_mid; ++l) {
                 wait_bar(&sm.acc_full[t], pacc, ctl, CTL_ABORT, ctr0, wait_ns);
                 pacc ^= 1u;
                 __syncwarp();  // tcgen05.ld below needs the whole warp converged
                 tc_fence_after();
-                const float *bl = bmid + l * W;
+                const float *bl = l ? bmid + (l - 1) * W : sm.zb;
                 uint32_t ra[32], rb[32];
                 tmem_ld32_async(taddr, ra);
                 tmem_wait_ld();
-                if (l + 1 < n_mid) {
+                if (l < n_mid) {
 #pragma unroll
                     for (int j = 0; j < W / 32; ++j) {
                         // the next chunk's load runs while this one is converted
@@ -586,7 +613,7 @@ void launch_bf16(const Item *items, int n_items, const float *p, long long n, fl
     }
 
 bool bf16_supported(int width) { return width == 64 || width == 128 || width == 256; }
-int bf16_max_mid() { return MAXMID; }
+int bf16_max_mid(int width) { return width == 256 ? maxmid_of<256>() : maxmid_of<128>(); }
 
 #define GH_BF16_T(T, ...)                                \
     if ((T) == 1) { constexpr int TT = 1; __VA_ARGS__; } \

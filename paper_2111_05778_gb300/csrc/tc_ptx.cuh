@@ -102,6 +102,13 @@ __device__ __forceinline__ unsigned long long sdesc(uint32_t saddr) {
            (1ull << 46) | (2ull << 61);
 }
 
+// K-major operand of 16 BF16 inputs per row, 32-byte swizzle, 8-row groups
+// 256 B apart.
+__device__ __forceinline__ unsigned long long sdesc32(uint32_t saddr) {
+    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(256 >> 4) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+
 // kind::f16 instruction descriptor: F32 accumulate, BF16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
