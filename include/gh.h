@@ -46,7 +46,7 @@ extern "C" {
 #define GH_ERR_CAPACITY 2      /* an output buffer was too small (see gh_mesh)  */
 #define GH_ERR_CUDA 3          /* a CUDA call failed; message has the details   */
 #define GH_ERR_NONFINITE 4     /* the SDB produced NaN or inf                   */
-#define GH_ERR_UNIMPLEMENTED 5 /* combination not supported by this build        */
+#define GH_ERR_UNIMPLEMENTED 5 /* combination not supported by the library        */
 #define GH_ERR_DEVICE 6        /* the GPU is not an sm_103 device               */
 
 /* ---- SDB kinds and their blob formats ---------------------------------- */
