@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                float *__restrict__ outv, unsigned long long wait_ns) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int KB = W / 64;
+    constexpr int RS = KB < NSTAGE ? KB : NSTAGE;  // K-blocks a phase can take over from the one before
     constexpr uint32_t STAGE_BYTES = W * 128;
     constexpr uint32_t TMEM_COLS = TILES * W < 32 ? 32 : TILES * W;
     constexpr uint32_t IDESC = idesc_bf16(TM, W);
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             bool fin[2] = {false, TILES < 2};
             uint32_t pir[2] = {0u, 0u};
             const uint8_t *src[2] = {nullptr, nullptr};
-            bool go = true;
+            bool go = true, keep = false;
             while (go && !(fin[0] && fin[1])) {
                 if (fin[t]) {
                     t ^= 1;
@@ -206,11 +207,18 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     }
                     src[t] = reinterpret_cast<const uint8_t *>(*(const uint16_t *volatile *)&sm.cur_wbf[t]);
                     // the layer-0 phase streams no weights
+                    keep = false;
                     lt[t] = 1;
                     if (!fin[t ^ 1]) t ^= 1;
                     continue;
                 }
-                for (int kb = 0; kb < KB; ++kb) {
+                // A phase right after the other tile's phase of the same layer
+                // of the same weights takes that phase's last RS K-blocks from
+                // the ring (they are still there) and streams only the others.
+                const bool reuse = keep;
+                keep = !reuse && !fin[t ^ 1] && lt[t ^ 1] == lt[t] && src[t ^ 1] == src[t];
+                for (int i = reuse ? RS : 0; i < KB; ++i) {
+                    const int kb = reuse ? i - RS : i;
                     const int st = (int)(issued % NSTAGE);
                     const uint32_t par = (uint32_t)(((issued / NSTAGE) & 1) ^ 1);
                     if (!wait_bar(&sm.empty[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
@@ -249,7 +257,8 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
             const unsigned long long ad0 = sdesc(su32(&sm.a[0][0][0])), ad1 = sdesc(su32(&sm.a[1][0][0]));
             const unsigned long long wd0 = sdesc(su32(sm.w[0]));
             const unsigned long long bd0 = sdesc32(su32(sm.b0[0])), bd1 = sdesc32(su32(sm.b0[1]));
-            bool go = true;
+            const uint16_t *w0 = nullptr, *w1 = nullptr;  // per tile: weights of its current item
+            bool go = true, keep = false;
             while (go && !(fin0 && fin1)) {
                 if (t ? fin1 : fin0) {
                     t ^= 1;
@@ -266,30 +275,49 @@ __global__ void __launch_bounds__(128 + 128 * TILES, 1)
                     if (!(t ? fin0 : fin1)) t ^= 1;
                     continue;
                 }
+                if (L == 0) {
+                    const uint16_t *w = *(const uint16_t *volatile *)&sm.cur_wbf[t];
+                    if (t) w1 = w;
+                    else w0 = w;
+                }
                 tc_fence_after();
                 const unsigned long long ad = t ? ad1 : ad0;
                 const uint32_t d = tmem + (uint32_t)(t * W);
                 if (L == 0) {
                     // layer 0: A0 in the first 16 inputs of the A operand's K-block 0
                     umma(d, ad, t ? bd1 : bd0, IDESC, 0u);
+                    keep = false;
                 } else {
-                for (int kb = 0; kb < KB; ++kb) {
-                    const int st = (int)(consumed % NSTAGE);
-                    const uint32_t par = (uint32_t)((consumed / NSTAGE) & 1);
-                    if (!mbar_try(&sm.full[st], par) &&
-                        !wait_bar(&sm.full[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
-                        go = false;
-                        break;
+                    // the same rule as the producer: after the other tile's phase of
+                    // this layer of the same weights, its last RS K-blocks (still in
+                    // the ring) come first, then the K-blocks streamed for this phase
+                    const bool reuse = keep;
+                    keep = !reuse && !(t ? fin0 : fin1) && (t ? lt0 : lt1) == L && (t ? w0 : w1) == (t ? w1 : w0);
+                    for (int i = 0; i < KB; ++i) {
+                        int kb, st;
+                        if (reuse && i < RS) {
+                            kb = KB - RS + i;
+                            st = (int)((consumed - RS + i) % NSTAGE);
+                        } else {
+                            kb = reuse ? i - RS : i;
+                            st = (int)(consumed % NSTAGE);
+                            const uint32_t par = (uint32_t)((consumed / NSTAGE) & 1);
+                            if (!mbar_try(&sm.full[st], par) &&
+                                !wait_bar(&sm.full[st], par, ctl, CTL_ABORT, ctr0, wait_ns)) {
+                                go = false;
+                                break;
+                            }
+                            ++consumed;
+                        }
+                        const unsigned long long a = ad + (unsigned long long)kb * A_KB;
+                        const unsigned long long b = wd0 + (unsigned long long)st * W_ST;
+                        umma(d, a, b, IDESC, i != 0);
+                        umma(d, a + 2, b + 2, IDESC, 1u);
+                        umma(d, a + 4, b + 4, IDESC, 1u);
+                        umma(d, a + 6, b + 6, IDESC, 1u);
+                        // a kept stage is released by the next phase, after its own use
+                        if (!(keep && i >= KB - RS)) umma_commit(&sm.empty[st]);
                     }
-                    const unsigned long long a = ad + (unsigned long long)kb * A_KB;
-                    const unsigned long long b = wd0 + (unsigned long long)st * W_ST;
-                    umma(d, a, b, IDESC, kb != 0);
-                    umma(d, a + 2, b + 2, IDESC, 1u);
-                    umma(d, a + 4, b + 4, IDESC, 1u);
-                    umma(d, a + 6, b + 6, IDESC, 1u);
-                    umma_commit(&sm.empty[st]);
-                    ++consumed;
-                }
                 }
                 if (!go) break;
                 umma_commit(&sm.acc_full[t]);
